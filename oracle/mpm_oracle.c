@@ -1,0 +1,513 @@
+/*
+ * mpm_oracle.c -- plain, single-threaded FP64 reference of one MLS-MPM time
+ * step with a Neo-Hookean material and rigid-tool collision handling, written
+ * from Sec. III-B (Eqs. 1-10) and Sec. III-C (Eqs. 11-19) of "Efficient
+ * Physically-based Simulation of Soft Bodies in Embodied Environment for
+ * Surgical Robot" (Yang et al., arXiv 2402.01181).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the checker for the CUDA library:
+ * only the tests, the package smoke check and the benchmark's CPU-baseline
+ * leg load it.  It shares no source, header, table or helper with the CUDA
+ * path, and the CUDA path never links or calls it.
+ *
+ * Everything is written in the order and notation of the paper: a step is
+ * P2G (Eqs. 1-3, with Eq. 5-6 for the stress), the grid operation (Eq. 7,
+ * boundary conditions, Eqs. 11-19 for tools), then G2P and advection
+ * (Eqs. 8-10, with Eq. 4 for F).  No blocking, sorting or fusion.
+ *
+ * Readings where the paper is silent or garbled (each listed in the design
+ * notes of the repository):
+ *   - Eq. 5 prints mu(F - F^T); the Neo-Hookean first Piola stress of the
+ *     cited MLS-MPM references is P = mu(F - F^-T) + lambda ln(J) F^-T, which
+ *     is what is evaluated here ("log" is the natural logarithm).
+ *   - Eq. 3 multiplies P(F') by F_p^T; the F stored on a particle is the one
+ *     already updated by Eq. 4 at the end of the previous G2P, so the stress
+ *     term uses P(F) F^T of that stored F.
+ *   - Quadratic B-spline weights (the paper defers w_ip to its references).
+ *   - Grid velocity is formed only where m_i > 0; gravity is added after
+ *     Eq. 7; sticky walls zero every component at nodes within `bound` nodes
+ *     of the domain faces, applied after tool handling.
+ *   - Tools use analytic distance functions (capsule, box) and their analytic,
+ *     normalised gradients in place of the sampled SDF of Eqs. 12-14; the
+ *     friction update of Eq. 18 is clamped at zero tangential speed; nodes
+ *     with v_n >= 0 are left unchanged; several tools are merged by minimum
+ *     distance with the lowest tool index winning ties (the z-buffer of
+ *     Sec. III-C).
+ *   - J <= 0 is clamped to 1e-6 inside ln and counted.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t n_grid;       /* nodes per axis; domain [0,1)^3, dx = 1/n_grid */
+    int32_t bound;        /* sticky wall band, in nodes */
+    double dt;            /* Delta t */
+    double gravity[3];
+    double E, nu, rho;    /* Young's modulus, Poisson ratio, density */
+    double V0;            /* V_p^0, equal for every particle; m_p = rho V_p^0 */
+    double theta;         /* collision threshold: contact if distance < theta */
+    double friction;      /* Coulomb coefficient mu of Eq. 18 */
+} orc_params;
+
+/* One rigid tool at one sub-step: world position of a reference-frame point
+ * is x = R x_ref + T (Eq. 11 inverts this). */
+typedef struct {
+    int32_t kind;         /* 0 capsule: dims = (radius, half-length along local y); 1 box: half extents */
+    int32_t pad;
+    double dims[3];
+    double R[9];          /* row-major rotation */
+    double T[3];
+    double u[3];          /* linear velocity of the reference point T */
+    double w[3];          /* angular velocity */
+} orc_tool;
+
+typedef struct {
+    int64_t j_clamped;    /* particles whose J <= 0 was clamped */
+    int64_t out_of_domain;/* particles whose stencil left the grid (clamped) */
+} orc_counters;
+
+/* ---------------------------------------------------------------- algebra */
+
+static void mat_mul(const double *A, const double *B, double *C) /* C = A B */
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+            C[3 * i + j] = s;
+        }
+}
+
+static double mat_det(const double *A)
+{
+    return A[0] * (A[4] * A[8] - A[5] * A[7])
+         - A[1] * (A[3] * A[8] - A[5] * A[6])
+         + A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+/* inverse transpose via the cofactor matrix: A^-T = cof(A) / det(A) */
+static void mat_inv_transpose(const double *A, double det, double *out)
+{
+    out[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+    out[1] = -(A[3] * A[8] - A[5] * A[6]) / det;
+    out[2] = (A[3] * A[7] - A[4] * A[6]) / det;
+    out[3] = -(A[1] * A[8] - A[2] * A[7]) / det;
+    out[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    out[5] = -(A[0] * A[7] - A[1] * A[6]) / det;
+    out[6] = (A[1] * A[5] - A[2] * A[4]) / det;
+    out[7] = -(A[0] * A[5] - A[2] * A[3]) / det;
+    out[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+}
+
+/* ------------------------------------------------------ material (Eq. 5-6) */
+
+/* Eq. 6: Lame parameters from Young's modulus and Poisson's ratio. */
+void orc_lame(double E, double nu, double *mu, double *lam)
+{
+    *mu = E / (2.0 * (1.0 + nu));
+    *lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+}
+
+/* Eq. 5 (reading: F^-T in the first term): first Piola-Kirchhoff stress.
+ * Returns 1 if J <= 0 had to be clamped inside ln. */
+int orc_piola(double mu, double lam, const double *F, double *P)
+{
+    double J = mat_det(F);
+    int clamped = 0;
+    double lnJ;
+    if (J <= 0.0) { clamped = 1; lnJ = log(1e-6); } else lnJ = log(J);
+    double FiT[9];
+    if (J == 0.0) { /* no inverse: fall back to the identity so P stays finite */
+        for (int i = 0; i < 9; ++i) FiT[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    } else {
+        mat_inv_transpose(F, J, FiT);
+    }
+    for (int i = 0; i < 9; ++i) P[i] = mu * (F[i] - FiT[i]) + lam * lnJ * FiT[i];
+    return clamped;
+}
+
+/* P(F) F^T, the product that enters Eq. 3. */
+int orc_piola_FT(double mu, double lam, const double *F, double *out)
+{
+    double P[9], FT[9];
+    int c = orc_piola(mu, lam, F, P);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) FT[3 * i + j] = F[3 * j + i];
+    mat_mul(P, FT, out);
+    return c;
+}
+
+/* ---------------------------------------------- quadratic B-spline weights */
+
+/* For one axis, with fx = x/dx - base in [0.5, 1.5), the weights of the nodes
+ * base, base+1, base+2 (the kernel the paper's references use for w_ip). */
+void orc_weights(double fx, double *w)
+{
+    w[0] = 0.5 * (1.5 - fx) * (1.5 - fx);
+    w[1] = 0.75 - (fx - 1.0) * (fx - 1.0);
+    w[2] = 0.5 * (fx - 0.5) * (fx - 0.5);
+}
+
+static int stencil_base(const orc_params *p, const double *xp, int *base, double *fx)
+{
+    int bad = 0;
+    for (int d = 0; d < 3; ++d) {
+        double s = xp[d] * (double)p->n_grid;
+        int b = (int)floor(s - 0.5);
+        if (b < 0) { b = 0; bad = 1; }
+        if (b > p->n_grid - 3) { b = p->n_grid - 3; bad = 1; }
+        base[d] = b;
+        fx[d] = s - (double)b;
+    }
+    return bad;
+}
+
+static inline int64_t node_index(int n, int i, int j, int k)
+{
+    return ((int64_t)i * n + j) * n + k;   /* grid[i][j][k], k fastest */
+}
+
+/* ------------------------------------------------------------ P2G (Eq. 1-3) */
+
+/* Scatter particle mass and momentum to the grid.  grid_m: n^3, grid_mv:
+ * n^3 x 3, both overwritten.  x, v: N x 3; C, F: N x 9 row-major. */
+void orc_p2g(const orc_params *p, int64_t N, const double *x, const double *v,
+             const double *C, const double *F, double *grid_m, double *grid_mv,
+             orc_counters *cnt)
+{
+    const int n = p->n_grid;
+    const double dx = 1.0 / n;
+    const double mp = p->rho * p->V0;
+    double mu, lam;
+    orc_lame(p->E, p->nu, &mu, &lam);
+    const int64_t nn = (int64_t)n * n * n;
+    memset(grid_m, 0, sizeof(double) * nn);
+    memset(grid_mv, 0, sizeof(double) * nn * 3);
+
+    for (int64_t q = 0; q < N; ++q) {
+        const double *xp = x + 3 * q, *vp = v + 3 * q, *Cp = C + 9 * q, *Fp = F + 9 * q;
+        int base[3];
+        double fx[3], w[3][3];
+        if (stencil_base(p, xp, base, fx) && cnt) cnt->out_of_domain++;
+        for (int d = 0; d < 3; ++d) orc_weights(fx[d], w[d]);
+        double PFt[9];
+        int c = orc_piola_FT(mu, lam, Fp, PFt);
+        if (c && cnt) cnt->j_clamped++;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    const double wip = w[0][i] * w[1][j] * w[2][k];
+                    const double xi_xp[3] = {(i - fx[0]) * dx, (j - fx[1]) * dx, (k - fx[2]) * dx};
+                    double mom[3];
+                    for (int a = 0; a < 3; ++a) {
+                        double Cd = 0.0, Sd = 0.0;
+                        for (int b = 0; b < 3; ++b) {
+                            Cd += Cp[3 * a + b] * xi_xp[b];
+                            Sd += PFt[3 * a + b] * xi_xp[b];
+                        }
+                        /* Eq. 3: f_ip = -(4/dx^2) V_p^0 P(F) F^T (x_i - x_p) */
+                        const double f = -(4.0 / (dx * dx)) * p->V0 * Sd;
+                        /* Eq. 1: m_p v_p + m_p C_p (x_i - x_p) + f_ip dt */
+                        mom[a] = mp * vp[a] + mp * Cd + f * p->dt;
+                    }
+                    const int64_t I = node_index(n, base[0] + i, base[1] + j, base[2] + k);
+                    for (int a = 0; a < 3; ++a) grid_mv[3 * I + a] += wip * mom[a];
+                    grid_m[I] += wip * mp;      /* Eq. 2 */
+                }
+    }
+}
+
+/* -------------------------------------------------- tool geometry (Eq. 11) */
+
+/* Rodrigues: rotation matrix of the rotation vector r. */
+void orc_rotvec_to_matrix(const double *r, double *R)
+{
+    const double th = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    const double K[9] = {0, -r[2], r[1], r[2], 0, -r[0], -r[1], r[0], 0};
+    double K2[9];
+    mat_mul(K, K, K2);
+    double a, b;
+    if (th < 1e-8) { a = 1.0 - th * th / 6.0; b = 0.5 - th * th / 24.0; }
+    else { a = sin(th) / th; b = (1.0 - cos(th)) / (th * th); }
+    for (int i = 0; i < 9; ++i) R[i] = ((i % 4 == 0) ? 1.0 : 0.0) + a * K[i] + b * K2[i];
+}
+
+/* Inverse of Rodrigues for angles in [0, pi]. */
+void orc_matrix_to_rotvec(const double *R, double *r)
+{
+    const double tr = R[0] + R[4] + R[8];
+    double c = 0.5 * (tr - 1.0);
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    const double th = acos(c);
+    const double s[3] = {R[7] - R[5], R[2] - R[6], R[3] - R[1]};  /* 2 sin(th) axis */
+    if (th < 1e-8) {
+        for (int d = 0; d < 3; ++d) r[d] = 0.5 * s[d];
+        return;
+    }
+    if (th < 3.14159265358979323846 - 1e-6) {
+        const double f = th / (2.0 * sin(th));
+        for (int d = 0; d < 3; ++d) r[d] = f * s[d];
+        return;
+    }
+    /* near pi: axis from the symmetric part R = 2 a a^T - I */
+    double a[3];
+    for (int d = 0; d < 3; ++d) {
+        double v = 0.5 * (R[4 * d] + 1.0);
+        a[d] = v > 0.0 ? sqrt(v) : 0.0;
+    }
+    int m = 0;
+    if (a[1] > a[m]) m = 1;
+    if (a[2] > a[m]) m = 2;
+    for (int d = 0; d < 3; ++d)
+        if (d != m) {
+            double sym = 0.5 * (R[3 * m + d] + R[3 * d + m]);
+            a[d] = sym / (2.0 * a[m]);
+        }
+    double nrm = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+    for (int d = 0; d < 3; ++d) r[d] = th * a[d] / nrm;
+}
+
+/* Tool frames for the sub-steps of one call that moves a tool uniformly from
+ * pose0 to pose1 (6-vectors: T, rotation vector) over nsub sub-steps of dt.
+ * Sub-step k uses the pose at fraction s = (k+1)/nsub:
+ *   T_k = T0 + s (T1 - T0),  R_k = exp(s phi) R0 with phi = log(R1 R0^T),
+ * and the rigid velocity field u + w x (x - T_k) with u = (T1 - T0)/(nsub dt),
+ * w = phi/(nsub dt).  With nsub = 1 this is the finite difference of
+ * consecutive poses. */
+void orc_tool_frames(int32_t kind, const double *dims, const double *pose0,
+                     const double *pose1, int32_t nsub, double dt, orc_tool *out)
+{
+    double R0[9], R1[9], R0T[9], Rrel[9], phi[3];
+    orc_rotvec_to_matrix(pose0 + 3, R0);
+    orc_rotvec_to_matrix(pose1 + 3, R1);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R0T[3 * i + j] = R0[3 * j + i];
+    mat_mul(R1, R0T, Rrel);
+    orc_matrix_to_rotvec(Rrel, phi);
+    const double span = nsub * dt;
+    for (int k = 0; k < nsub; ++k) {
+        const double s = (double)(k + 1) / (double)nsub;
+        orc_tool *t = out + k;
+        t->kind = kind;
+        t->pad = 0;
+        for (int d = 0; d < 3; ++d) t->dims[d] = dims[d];
+        double rs[3] = {s * phi[0], s * phi[1], s * phi[2]}, Rs[9];
+        orc_rotvec_to_matrix(rs, Rs);
+        mat_mul(Rs, R0, t->R);
+        for (int d = 0; d < 3; ++d) {
+            t->T[d] = pose0[d] + s * (pose1[d] - pose0[d]);
+            t->u[d] = (pose1[d] - pose0[d]) / span;
+            t->w[d] = phi[d] / span;
+        }
+    }
+}
+
+/* Signed distance of a reference-frame point to the tool surface and the
+ * outward unit normal there (analytic stand-in for Eqs. 12-14). */
+double orc_sdf(int32_t kind, const double *dims, const double *p, double *nrm)
+{
+    if (kind == 0) {                  /* capsule around the local y segment */
+        double c = p[1];
+        if (c > dims[1]) c = dims[1];
+        if (c < -dims[1]) c = -dims[1];
+        const double q[3] = {p[0], p[1] - c, p[2]};
+        const double L = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+        if (L > 0.0) { nrm[0] = q[0] / L; nrm[1] = q[1] / L; nrm[2] = q[2] / L; }
+        else { nrm[0] = 0.0; nrm[1] = 1.0; nrm[2] = 0.0; }
+        return L - dims[0];
+    }
+    /* box with half extents dims */
+    double q[3], o[3], on = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        q[d] = fabs(p[d]) - dims[d];
+        o[d] = q[d] > 0.0 ? q[d] : 0.0;
+        on += o[d] * o[d];
+    }
+    on = sqrt(on);
+    if (on > 0.0) {
+        for (int d = 0; d < 3; ++d) nrm[d] = (p[d] < 0.0 ? -1.0 : 1.0) * o[d] / on;
+        return on;
+    }
+    int a = 0;
+    if (q[1] > q[a]) a = 1;
+    if (q[2] > q[a]) a = 2;
+    nrm[0] = nrm[1] = nrm[2] = 0.0;
+    nrm[a] = p[a] < 0.0 ? -1.0 : 1.0;
+    return q[a];
+}
+
+/* ------------------------------------------- grid operation (Eq. 7, 11-19) */
+
+/* grid_v: n^3 x 3 output.  contact (optional, n^3): index of the tool whose
+ * projection was applied, -1 otherwise.  margin (optional, n^3): distance of
+ * this node's floating-point decisions from a branch point -- min over
+ * |d - theta|, |v_n| (if in contact) and the gap to the second-closest tool;
+ * +inf where no decision depends on the tool. */
+void orc_grid_update(const orc_params *p, const orc_tool *tools, int32_t ntools,
+                     const double *grid_m, const double *grid_mv, double *grid_v,
+                     int32_t *contact, double *margin)
+{
+    const int n = p->n_grid;
+    const double dx = 1.0 / n;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < n; ++k) {
+                const int64_t I = node_index(n, i, j, k);
+                double v[3] = {0.0, 0.0, 0.0};
+                int32_t hit = -1;
+                double mg = INFINITY;
+                if (grid_m[I] > 0.0) {
+                    for (int a = 0; a < 3; ++a)
+                        v[a] = grid_mv[3 * I + a] / grid_m[I] + p->dt * p->gravity[a];  /* Eq. 7 + gravity */
+                    if (ntools > 0) {
+                        const double xw[3] = {i * dx, j * dx, k * dx};
+                        double dmin = INFINITY, d2 = INFINITY, nref_best[3] = {0, 0, 0};
+                        int id = -1;
+                        for (int t = 0; t < ntools; ++t) {
+                            const orc_tool *tl = tools + t;
+                            double xr[3], nr[3];
+                            for (int a = 0; a < 3; ++a) {   /* Eq. 11: R^-1 (x - T) */
+                                double s = 0.0;
+                                for (int b = 0; b < 3; ++b) s += tl->R[3 * b + a] * (xw[b] - tl->T[b]);
+                                xr[a] = s;
+                            }
+                            const double d = orc_sdf(tl->kind, tl->dims, xr, nr);
+                            if (d < dmin) {
+                                d2 = dmin;
+                                dmin = d; id = t;
+                                nref_best[0] = nr[0]; nref_best[1] = nr[1]; nref_best[2] = nr[2];
+                            } else if (d < d2) {
+                                d2 = d;
+                            }
+                        }
+                        mg = fabs(dmin - p->theta);
+                        if (d2 < INFINITY && d2 - dmin < mg) mg = d2 - dmin;
+                        if (dmin < p->theta) {
+                            const orc_tool *tl = tools + id;
+                            double nw[3], r[3], vco[3], vrel[3];
+                            for (int a = 0; a < 3; ++a) {
+                                nw[a] = 0.0;
+                                for (int b = 0; b < 3; ++b) nw[a] += tl->R[3 * a + b] * nref_best[b];
+                                r[a] = xw[a] - tl->T[a];
+                            }
+                            vco[0] = tl->u[0] + tl->w[1] * r[2] - tl->w[2] * r[1];
+                            vco[1] = tl->u[1] + tl->w[2] * r[0] - tl->w[0] * r[2];
+                            vco[2] = tl->u[2] + tl->w[0] * r[1] - tl->w[1] * r[0];
+                            double vn = 0.0;
+                            for (int a = 0; a < 3; ++a) { vrel[a] = v[a] - vco[a]; vn += vrel[a] * nw[a]; }  /* Eq. 15-16 */
+                            if (fabs(vn) < mg) mg = fabs(vn);
+                            if (vn < 0.0) {
+                                double vt[3], vtn = 0.0;
+                                for (int a = 0; a < 3; ++a) { vt[a] = vrel[a] - vn * nw[a]; vtn += vt[a] * vt[a]; }  /* Eq. 17 */
+                                vtn = sqrt(vtn);
+                                double scale = 0.0;             /* Eq. 18, clamped */
+                                if (vtn > 0.0) {
+                                    const double s = vtn + p->friction * vn;
+                                    scale = s > 0.0 ? s / vtn : 0.0;
+                                    if (fabs(s) < mg) mg = fabs(s);
+                                }
+                                for (int a = 0; a < 3; ++a) v[a] = scale * vt[a] + vco[a];  /* Eq. 19 */
+                            }
+                            hit = id;
+                        }
+                    }
+                    const int b = p->bound;
+                    if (i < b || j < b || k < b || i >= n - b || j >= n - b || k >= n - b) {
+                        v[0] = v[1] = v[2] = 0.0;          /* sticky walls */
+                        mg = INFINITY;
+                        hit = -1;
+                    }
+                }
+                for (int a = 0; a < 3; ++a) grid_v[3 * I + a] = v[a];
+                if (contact) contact[I] = hit;
+                if (margin) margin[I] = mg;
+            }
+}
+
+/* ---------------------------------------------------- G2P (Eq. 4, 8-10) */
+
+/* Gather grid velocities back to the particles and advect them; updates
+ * x, v, C, F in place. */
+void orc_g2p(const orc_params *p, const double *grid_v, int64_t N, double *x,
+             double *v, double *C, double *F, orc_counters *cnt)
+{
+    const int n = p->n_grid;
+    const double dx = 1.0 / n;
+    for (int64_t q = 0; q < N; ++q) {
+        double *xp = x + 3 * q, *vp = v + 3 * q, *Cp = C + 9 * q, *Fp = F + 9 * q;
+        int base[3];
+        double fx[3], w[3][3];
+        if (stencil_base(p, xp, base, fx) && cnt) cnt->out_of_domain++;
+        for (int d = 0; d < 3; ++d) orc_weights(fx[d], w[d]);
+        double vnew[3] = {0, 0, 0}, B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    const double wip = w[0][i] * w[1][j] * w[2][k];
+                    const double xi_xp[3] = {(i - fx[0]) * dx, (j - fx[1]) * dx, (k - fx[2]) * dx};
+                    const int64_t I = node_index(n, base[0] + i, base[1] + j, base[2] + k);
+                    const double *vi = grid_v + 3 * I;
+                    for (int a = 0; a < 3; ++a) {
+                        vnew[a] += wip * vi[a];                         /* Eq. 8 */
+                        for (int b = 0; b < 3; ++b) B[3 * a + b] += wip * vi[a] * xi_xp[b];
+                    }
+                }
+        for (int a = 0; a < 9; ++a) Cp[a] = 4.0 / (dx * dx) * B[a];     /* Eq. 9 */
+        double IdtC[9], Fn[9];
+        for (int a = 0; a < 9; ++a) IdtC[a] = ((a % 4 == 0) ? 1.0 : 0.0) + p->dt * Cp[a];
+        mat_mul(IdtC, Fp, Fn);                                          /* Eq. 4 */
+        memcpy(Fp, Fn, sizeof Fn);
+        for (int a = 0; a < 3; ++a) {
+            vp[a] = vnew[a];
+            xp[a] += p->dt * vnew[a];                                   /* Eq. 10 */
+        }
+    }
+}
+
+/* ------------------------------------------------------------- full step */
+
+/* One sub-step: P2G, grid operation, G2P.  scratch must hold 7 n^3 doubles.
+ * tools: ntools frames for this sub-step. */
+void orc_step(const orc_params *p, const orc_tool *tools, int32_t ntools, int64_t N,
+              double *x, double *v, double *C, double *F, double *scratch,
+              orc_counters *cnt)
+{
+    const int64_t nn = (int64_t)p->n_grid * p->n_grid * p->n_grid;
+    double *gm = scratch, *gmv = scratch + nn, *gv = scratch + 4 * nn;
+    orc_p2g(p, N, x, v, C, F, gm, gmv, cnt);
+    orc_grid_update(p, tools, ntools, gm, gmv, gv, NULL, NULL);
+    orc_g2p(p, gv, N, x, v, C, F, cnt);
+}
+
+/* nsteps sub-steps; tools holds nsteps * ntools frames (sub-step major). */
+void orc_run(const orc_params *p, const orc_tool *tools, int32_t ntools, int32_t nsteps,
+             int64_t N, double *x, double *v, double *C, double *F, orc_counters *cnt)
+{
+    const int64_t nn = (int64_t)p->n_grid * p->n_grid * p->n_grid;
+    double *scratch = (double *)malloc(sizeof(double) * 7 * nn);
+    if (!scratch) return;
+    for (int s = 0; s < nsteps; ++s)
+        orc_step(p, tools + (int64_t)s * ntools, ntools, N, x, v, C, F, scratch, cnt);
+    free(scratch);
+}
+
+/* Grid-block key of each particle: the linear index (x fastest) of the
+ * 4x4x4-cell block containing base = floor(x/dx - 0.5), computed from the
+ * FP32 positions the GPU holds.  Domain clamping as in the stencil. */
+void orc_block_keys(int32_t n_grid, int64_t N, const float *x, uint32_t *keys)
+{
+    const int nb = n_grid / 4;
+    for (int64_t q = 0; q < N; ++q) {
+        int b[3];
+        for (int d = 0; d < 3; ++d) {
+            int c = (int)floor((double)x[3 * q + d] * (double)n_grid - 0.5);
+            if (c < 0) c = 0;
+            if (c > n_grid - 3) c = n_grid - 3;
+            b[d] = c / 4;
+        }
+        keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));
+    }
+}

@@ -1,0 +1,306 @@
+"""ctypes front end of the FP64 MLS-MPM oracle (oracle/mpm_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the
+benchmark's CPU-baseline leg use this module; the CUDA library never does.
+It builds the C file with gcc (strict IEEE double: no fast-math, no FMA
+contraction, so results agree between x86-64 and aarch64 hosts) into
+oracle/_build/ and wraps each entry point with numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mpm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libmpm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library if it is missing or stale."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(ct.Structure):
+    _fields_ = [("n_grid", ct.c_int32), ("bound", ct.c_int32), ("dt", ct.c_double),
+                ("gravity", ct.c_double * 3), ("E", ct.c_double), ("nu", ct.c_double),
+                ("rho", ct.c_double), ("V0", ct.c_double), ("theta", ct.c_double),
+                ("friction", ct.c_double)]
+
+
+class ToolFrame(ct.Structure):
+    _fields_ = [("kind", ct.c_int32), ("pad", ct.c_int32), ("dims", ct.c_double * 3),
+                ("R", ct.c_double * 9), ("T", ct.c_double * 3), ("u", ct.c_double * 3),
+                ("w", ct.c_double * 3)]
+
+
+class Counters(ct.Structure):
+    _fields_ = [("j_clamped", ct.c_int64), ("out_of_domain", ct.c_int64)]
+
+
+_D = ct.POINTER(ct.c_double)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            # ORACLE_LIB lets the mutation tests load a deliberately broken copy.
+            L = ct.CDLL(os.environ.get("ORACLE_LIB") or build())
+            P = ct.POINTER(Params)
+            TF = ct.POINTER(ToolFrame)
+            CN = ct.POINTER(Counters)
+            L.orc_lame.argtypes = [ct.c_double, ct.c_double, _D, _D]
+            L.orc_piola.argtypes = [ct.c_double, ct.c_double, _D, _D]
+            L.orc_piola.restype = ct.c_int
+            L.orc_piola_FT.argtypes = [ct.c_double, ct.c_double, _D, _D]
+            L.orc_piola_FT.restype = ct.c_int
+            L.orc_weights.argtypes = [ct.c_double, _D]
+            L.orc_p2g.argtypes = [P, ct.c_int64, _D, _D, _D, _D, _D, _D, CN]
+            L.orc_rotvec_to_matrix.argtypes = [_D, _D]
+            L.orc_matrix_to_rotvec.argtypes = [_D, _D]
+            L.orc_tool_frames.argtypes = [ct.c_int32, _D, _D, _D, ct.c_int32, ct.c_double, TF]
+            L.orc_sdf.argtypes = [ct.c_int32, _D, _D, _D]
+            L.orc_sdf.restype = ct.c_double
+            L.orc_grid_update.argtypes = [P, TF, ct.c_int32, _D, _D, _D,
+                                          ct.POINTER(ct.c_int32), _D]
+            L.orc_g2p.argtypes = [P, _D, ct.c_int64, _D, _D, _D, _D, CN]
+            L.orc_step.argtypes = [P, TF, ct.c_int32, ct.c_int64, _D, _D, _D, _D, _D, CN]
+            L.orc_run.argtypes = [P, TF, ct.c_int32, ct.c_int32, ct.c_int64, _D, _D, _D, _D, CN]
+            L.orc_block_keys.argtypes = [ct.c_int32, ct.c_int64, ct.POINTER(ct.c_float),
+                                         ct.POINTER(ct.c_uint32)]
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a, shape=None):
+    out = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        out = out.reshape(shape)
+    return out
+
+
+# ------------------------------------------------------------------ params
+
+@dataclass
+class OracleParams:
+    n_grid: int
+    dt: float
+    E: float
+    nu: float
+    rho: float
+    V0: float
+    gravity: Sequence[float] = (0.0, -9.8, 0.0)
+    bound: int = 3
+    theta: float = 0.0
+    friction: float = 0.0
+
+    def c(self) -> Params:
+        p = Params()
+        p.n_grid = self.n_grid
+        p.bound = self.bound
+        p.dt = self.dt
+        for i in range(3):
+            p.gravity[i] = self.gravity[i]
+        p.E, p.nu, p.rho, p.V0 = self.E, self.nu, self.rho, self.V0
+        p.theta, p.friction = self.theta, self.friction
+        return p
+
+    @property
+    def mass(self) -> float:
+        return self.rho * self.V0
+
+    @staticmethod
+    def from_scene(sc) -> "OracleParams":
+        return OracleParams(n_grid=sc.n_grid, dt=sc.dt, E=sc.E, nu=sc.nu, rho=sc.rho,
+                            V0=sc.particle_volume, gravity=tuple(sc.gravity), bound=sc.bound,
+                            theta=sc.theta, friction=sc.friction)
+
+
+# -------------------------------------------------------------- primitives
+
+def lame(E, nu):
+    mu, lam = ct.c_double(), ct.c_double()
+    lib().orc_lame(E, nu, ct.byref(mu), ct.byref(lam))
+    return mu.value, lam.value
+
+
+def piola(mu, lam, F):
+    F = _f64(F, (9,))
+    P = np.zeros(9)
+    lib().orc_piola(mu, lam, _dp(F), _dp(P))
+    return P.reshape(3, 3)
+
+
+def piola_FT(mu, lam, F):
+    F = _f64(F, (9,))
+    P = np.zeros(9)
+    lib().orc_piola_FT(mu, lam, _dp(F), _dp(P))
+    return P.reshape(3, 3)
+
+
+def weights(fx):
+    w = np.zeros(3)
+    lib().orc_weights(float(fx), _dp(w))
+    return w
+
+
+def rotvec_to_matrix(r):
+    r = _f64(r, (3,))
+    R = np.zeros(9)
+    lib().orc_rotvec_to_matrix(_dp(r), _dp(R))
+    return R.reshape(3, 3)
+
+
+def matrix_to_rotvec(R):
+    R = _f64(R, (9,))
+    r = np.zeros(3)
+    lib().orc_matrix_to_rotvec(_dp(R), _dp(r))
+    return r
+
+
+def sdf(kind, dims, p):
+    dims = _f64(dims, (3,))
+    p = _f64(p, (3,))
+    n = np.zeros(3)
+    d = lib().orc_sdf(int(kind), _dp(dims), _dp(p), _dp(n))
+    return d, n
+
+
+def tool_frames(shape, pose0, pose1, nsub, dt):
+    """Frames for one tool over one call of nsub sub-steps (see the C file)."""
+    shape = np.asarray(shape, dtype=np.float64)
+    kind = int(shape[0])
+    dims = _f64(shape[1:4])
+    arr = (ToolFrame * nsub)()
+    lib().orc_tool_frames(kind, _dp(dims), _dp(_f64(pose0, (6,))), _dp(_f64(pose1, (6,))),
+                          int(nsub), float(dt), arr)
+    return arr
+
+
+def frames_for_steps(tools, s0, nsub, dt, call_len=None):
+    """Sub-step-major ToolFrame array for sub-steps s0 .. s0+nsub-1 of a scene's
+    scripted tools, when the simulation is driven by calls of call_len
+    sub-steps (default: one call covering all nsub) whose target pose is the
+    scripted pose at the end of the call."""
+    if not tools:
+        return (ToolFrame * 1)(), 0
+    call_len = call_len or nsub
+    nt = len(tools)
+    out = (ToolFrame * (nsub * nt))()
+    s = s0
+    while s < s0 + nsub:
+        m = min(call_len, s0 + nsub - s)
+        for t, tool in enumerate(tools):
+            fr = tool_frames(tool.shape, tool.pose(s - 1), tool.pose(s + m - 1), m, dt)
+            for k in range(m):
+                ct.memmove(ct.byref(out, ((s - s0 + k) * nt + t) * ct.sizeof(ToolFrame)),
+                           ct.byref(fr, k * ct.sizeof(ToolFrame)), ct.sizeof(ToolFrame))
+        s += m
+    return out, nt
+
+
+# ------------------------------------------------------------- the method
+
+class State:
+    """FP64 particle state (x, v, C, F) in particle-id order."""
+
+    def __init__(self, x, v=None, C=None, F=None):
+        n = np.asarray(x).shape[0]
+        self.x = _f64(x, (n, 3)).copy()
+        self.v = np.zeros((n, 3)) if v is None else _f64(v, (n, 3)).copy()
+        self.C = np.zeros((n, 9)) if C is None else _f64(C, (n, 9)).copy()
+        self.F = np.tile(np.eye(3).reshape(1, 9), (n, 1)) if F is None else _f64(F, (n, 9)).copy()
+        self.counters = Counters()
+
+    @property
+    def n(self):
+        return self.x.shape[0]
+
+    def copy(self):
+        s = State(self.x, self.v, self.C, self.F)
+        s.counters.j_clamped = self.counters.j_clamped
+        s.counters.out_of_domain = self.counters.out_of_domain
+        return s
+
+
+def p2g(prm: OracleParams, st: State):
+    n = prm.n_grid
+    gm = np.zeros(n ** 3)
+    gmv = np.zeros(n ** 3 * 3)
+    lib().orc_p2g(ct.byref(prm.c()), st.n, _dp(st.x), _dp(st.v), _dp(st.C), _dp(st.F),
+                  _dp(gm), _dp(gmv), ct.byref(st.counters))
+    return gm.reshape(n, n, n), gmv.reshape(n, n, n, 3)
+
+
+def grid_update(prm: OracleParams, gm, gmv, frames=None, ntools=0):
+    n = prm.n_grid
+    gm = _f64(gm, (n ** 3,))
+    gmv = _f64(gmv, (n ** 3 * 3,))
+    gv = np.zeros(n ** 3 * 3)
+    contact = np.zeros(n ** 3, dtype=np.int32)
+    margin = np.zeros(n ** 3)
+    if frames is None:
+        frames = (ToolFrame * 1)()
+        ntools = 0
+    lib().orc_grid_update(ct.byref(prm.c()), frames, int(ntools), _dp(gm), _dp(gmv), _dp(gv),
+                          contact.ctypes.data_as(ct.POINTER(ct.c_int32)), _dp(margin))
+    return gv.reshape(n, n, n, 3), contact.reshape(n, n, n), margin.reshape(n, n, n)
+
+
+def g2p(prm: OracleParams, st: State, gv):
+    n = prm.n_grid
+    gv = _f64(gv, (n ** 3 * 3,))
+    lib().orc_g2p(ct.byref(prm.c()), _dp(gv), st.n, _dp(st.x), _dp(st.v), _dp(st.C),
+                  _dp(st.F), ct.byref(st.counters))
+
+
+def run(prm: OracleParams, st: State, nsteps: int, frames=None, ntools=0):
+    """nsteps sub-steps in place; frames is sub-step-major (nsteps * ntools)."""
+    if frames is None or ntools == 0:
+        frames = (ToolFrame * 1)()
+        ntools = 0
+    lib().orc_run(ct.byref(prm.c()), frames, int(ntools), int(nsteps), st.n, _dp(st.x),
+                  _dp(st.v), _dp(st.C), _dp(st.F), ct.byref(st.counters))
+
+
+def block_keys(n_grid: int, x32: np.ndarray) -> np.ndarray:
+    x32 = np.ascontiguousarray(x32, dtype=np.float32).reshape(-1, 3)
+    keys = np.zeros(x32.shape[0], dtype=np.uint32)
+    lib().orc_block_keys(int(n_grid), x32.shape[0], x32.ctypes.data_as(ct.POINTER(ct.c_float)),
+                         keys.ctypes.data_as(ct.POINTER(ct.c_uint32)))
+    return keys
+
+
+def sorted_order(keys: np.ndarray, previous: Optional[np.ndarray] = None) -> np.ndarray:
+    """Stable counting-sort order of particle ids by block key.
+
+    previous: the logical order before this sort (ids); None means id order.
+    Returns the ids in sorted order: ascending key, ties kept in their
+    previous relative order.  numpy's stable sort is the library step.
+    """
+    if previous is None:
+        previous = np.arange(keys.shape[0], dtype=np.int64)
+    previous = np.asarray(previous, dtype=np.int64)
+    idx = np.argsort(keys[previous], kind="stable")
+    return previous[idx]

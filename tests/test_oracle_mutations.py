@@ -1,0 +1,52 @@
+"""The oracle's pins have teeth: plant a plausible mistake in a copy of the
+oracle source (a dropped term, a wrong sign, a transposed operand, a wrong
+index, the garbled printed form of Eq. 5), build it, and check that the pin
+suite fails on it.  Runs on the CPU only; the real oracle is untouched."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mpm_oracle.c")
+
+MUTATIONS = {
+    "Eq5 printed F - F^T": ("mu * (F[i] - FiT[i])", "mu * (F[i] - F[3 * (i % 3) + i / 3])"),
+    "stress impulse sign": ("const double f = -(4.0 / (dx * dx))", "const double f = (4.0 / (dx * dx))"),
+    "stress uses F^T F": ("mat_mul(P, FT, out);", "mat_mul(FT, P, out);"),
+    "dropped affine term": ("mom[a] = mp * vp[a] + mp * Cd + f * p->dt;", "mom[a] = mp * vp[a] + f * p->dt;"),
+    "transposed C in P2G": ("Cd += Cp[3 * a + b] * xi_xp[b];", "Cd += Cp[3 * b + a] * xi_xp[b];"),
+    "transposed C in G2P": ("B[3 * a + b] += wip * vi[a] * xi_xp[b];", "B[3 * b + a] += wip * vi[a] * xi_xp[b];"),
+    "F update order": ("mat_mul(IdtC, Fp, Fn);", "mat_mul(Fp, IdtC, Fn);"),
+    "weight w2": ("w[2] = 0.5 * (fx - 0.5) * (fx - 0.5);", "w[2] = 0.5 * (fx - 0.4) * (fx - 0.4);"),
+    "node index order": ("return ((int64_t)i * n + j) * n + k;", "return ((int64_t)k * n + j) * n + i;"),
+    "no gravity": ("+ p->dt * p->gravity[a];  /* Eq. 7", ";  /* Eq. 7"),
+    "advect with old v": ("vp[a] = vnew[a];\n            xp[a] += p->dt * vnew[a];",
+                          "xp[a] += p->dt * vp[a];\n            vp[a] = vnew[a];"),
+    "x_ref uses R not R^T": ("s += tl->R[3 * b + a] * (xw[b] - tl->T[b]);", "s += tl->R[3 * a + b] * (xw[b] - tl->T[b]);"),
+    "friction not clamped": ("scale = s > 0.0 ? s / vtn : 0.0;", "scale = s / vtn;"),
+    "projects separating nodes": ("if (vn < 0.0) {", "if (vn < 1e30) {"),
+    "normal not rotated": ("nw[a] += tl->R[3 * a + b] * nref_best[b];", "nw[a] += tl->R[3 * b + a] * nref_best[b];"),
+    "tool velocity drops spin": ("vco[0] = tl->u[0] + tl->w[1] * r[2] - tl->w[2] * r[1];", "vco[0] = tl->u[0];"),
+    "z-buffer picks farthest": ("if (d < dmin) {", "if (d > dmin || dmin == INFINITY) {"),
+    "walls ignored": ("v[0] = v[1] = v[2] = 0.0;          /* sticky walls */", ";"),
+    "block key axis order": ("keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));", "keys[q] = (uint32_t)(b[2] + nb * (b[1] + nb * b[0]));"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation anchor must be unique: " + name
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, new))
+    lib = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", str(lib), str(mutated), "-lm"])
+    env = dict(os.environ, ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "planted mistake '%s' passed every pin" % name
