@@ -1,0 +1,365 @@
+"""Benchmark of the GB300 MLS-MPM step.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                [--workload block1m|slab30k|block8m|cube8k] [--substeps S]
+                [--pipeline fused|split]
+
+A benchmark step is one call of mpm_step with S sub-steps (default 25, one
+frame of the paper's simulation loop: 25 sub-steps per rendered frame) with
+the scripted tool pose set before it.  The metric is particle-steps/s:
+particles x sub-steps / time, summed over ranks.  `value` times the frames
+with the state resident on the GPU (CUDA events on the simulation stream,
+L2 flushed by a 256 MB write between frames); `e2e` times the same frames
+through the C ABI with host buffers: the tool pose goes in from the host and
+every frame's particle positions come back to pinned host memory.
+
+--gpus N > 1 (under torchrun) runs N independent replicas of the scene, one
+per GPU (the single-scene step does not shard; see the design notes), and
+reports the aggregate over ranks from the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (oracle/) on the host cores on a
+bounded sample of the same workload; there is no other implementation of
+this method to compare with.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2402_01181_gb300 import scenes  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="block1m", choices=sorted(scenes.SCENES))
+    ap.add_argument("--substeps", type=int, default=25)
+    ap.add_argument("--pipeline", default="fused", choices=["fused", "split"])
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 30K slab line")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("kernel_fused.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2402_01181_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ GPU workload
+
+def run_gpu_workload(name, args, rank, device, barrier, max_over_ranks, with_e2e=True, with_roofline=True,
+                     steps=None):
+    import torch
+    from paper_2402_01181_gb300 import mpm
+    steps = steps or args.steps
+    S = args.substeps
+    sc = scenes.SCENES[name](seed=rank)
+    pipe = mpm.MPM_PIPELINE_FUSED if args.pipeline == "fused" else mpm.MPM_PIPELINE_SPLIT
+    stream = torch.cuda.current_stream(device)
+    sim = mpm.sim_from_scene(sc, pipeline=pipe)
+    tool_frames = [(t, tool) for t, tool in enumerate(sc.tools)]
+    s_next = [0]
+
+    def frame():
+        s = s_next[0]
+        for t, tool in tool_frames:
+            sim.set_tool(t, tool.pose(s + S - 1), tool.shape)
+        sim.step(S)
+        s_next[0] = s + S
+
+    grid = sim.read_grid()
+    active_nodes = int((grid[..., 0] > 0).sum())
+    del grid
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    for _ in range(args.warmup):
+        frame()
+    sim.synchronize()
+    barrier()
+    torch.cuda.synchronize(device)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with ClockSampler(device) as clk:
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            frame()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(device)
+    barrier()
+    st = sim.status()
+    if st != mpm.MPM_OK:
+        raise RuntimeError("device error after timed region: %s" % mpm.mpm_last_error())
+    frame_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = max_over_ranks(sum(frame_ms))
+    res = {"n": sc.n, "n_grid": sc.n_grid, "frame_ms": frame_ms, "t_ms": t_ms, "clocks": clk.summary(),
+           "active_nodes": active_nodes, "steps": steps}
+
+    if with_e2e:
+        # end to end through the C ABI with host buffers
+        import ctypes as ct
+        host_x = torch.empty((sc.n, 3), dtype=torch.float32, pin_memory=True)
+        xp = ct.c_void_p(host_x.data_ptr())
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            frame()
+            mpm.check(mpm.mpm_read_particles(sim.h, xp, None, None, None, 0))
+        t_e2e = max_over_ranks((time.perf_counter() - t0) * 1e3)
+        res["t_e2e_ms"] = t_e2e
+        ntools = len(sc.tools)
+        res["h2d"] = 112 * mpm.MPM_MAX_TOOLS * S if ntools else 0     # tool frames of the call
+        res["d2h"] = sc.n * 12 + 4                                     # positions + status word
+    sim.close()
+    return res
+
+
+def algorithmic_bytes_per_particle_step(n, active_nodes, S):
+    """Minimum DRAM traffic of one fused sub-step, per particle: the particle
+    state is read and written once (x, id: 16 B; F: 36 B; twice = 104 B); each
+    active grid node is read once (16 B), accumulated into once (16 B) and
+    cleared once (16 B); v and C (48 B) are written once per call."""
+    return 104.0 + 48.0 * active_nodes / n + 48.0 / S
+
+
+# --------------------------------------------------------------- oracle arm
+
+def time_oracle(name, budget_s, rank_seed=0, max_steps=50):
+    """Time the FP64 oracle on the workload; returns (particle-steps/s, sample)."""
+    from oracle import oracle as O
+    sc = scenes.SCENES[name](seed=rank_seed)
+    prm = O.OracleParams.from_scene(sc)
+    st = O.State(sc.x, sc.v, sc.C, sc.F)
+    done, t0 = 0, time.perf_counter()
+    while done < max_steps:
+        frames, nt = O.frames_for_steps(sc.tools, done, 1, sc.dt, 1)
+        O.run(prm, st, 1, frames, nt)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return sc.n * done / el, "%d sub-steps of the full %s workload (%d particles, %d^3 grid)" % (
+        done, name, sc.n, sc.n_grid)
+
+
+def reference_main(args):
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            dist.destroy_process_group()
+            return
+    budget = 8.0
+    vals = []
+    for _ in range(args.warmup):
+        time_oracle(args.workload, budget / 4, max_steps=1)
+    t0 = time.perf_counter()
+    sample = ""
+    for _ in range(args.steps):
+        v, sample = time_oracle(args.workload, budget, max_steps=3)
+        vals.append(v)
+    el = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "impl": "FP64 single-threaded C oracle"},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_main(args)
+    import torch
+    world, rank, local = dist_env()
+    device = local if torch.cuda.device_count() > local else 0
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", device))
+
+        def barrier():
+            dist.barrier()
+
+        def max_over_ranks(v):
+            t = torch.tensor([float(v)], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+    else:
+        def barrier():
+            pass
+
+        def max_over_ranks(v):
+            return float(v)
+
+    import __graft_entry__ as ge
+    ge.build()
+    S = args.substeps
+    main_res = run_gpu_workload(args.workload, args, rank, device, barrier, max_over_ranks)
+    n_units = main_res["n"] * S * args.steps * world
+    value = n_units / (main_res["t_ms"] / 1e3)
+    ms_per_step = main_res["t_ms"] / args.steps
+    second = None
+    if not args.no_secondary and args.workload != "slab30k":
+        r2 = run_gpu_workload("slab30k", args, rank, device, barrier, max_over_ranks, with_e2e=True,
+                              steps=max(args.steps, 20))
+        second = {"workload": "slab30k", "n_particles": r2["n"], "n_grid": r2["n_grid"],
+                  "value": r2["n"] * S * r2["steps"] * world / (r2["t_ms"] / 1e3),
+                  "ms_per_step": r2["t_ms"] / r2["steps"],
+                  "e2e": r2["n"] * S * r2["steps"] * world / (r2["t_e2e_ms"] / 1e3)}
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peak()
+    bpp = algorithmic_bytes_per_particle_step(main_res["n"], main_res["active_nodes"], S)
+    launch_ms = main_res["t_ms"] / (args.steps * S)      # per fused launch (frame time / sub-steps)
+    achieved = bpp * main_res["n"] / (launch_ms / 1e3) / 1e9
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            tr = json.load(fh)
+        if tr.get("kernel_sha") == kernel_source_sha() and tr.get("workload") == args.workload:
+            traffic = tr.get("bytes_per_launch")
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_fused_step" if args.pipeline == "fused"
+                else "p2g+grid+g2p", "algorithmic_bytes_per_particle_step": bpp,
+                "launch_us": launch_ms * 1e3}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, sample = time_oracle(args.workload, 15.0)
+        cpu = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
+    e2e_val = main_res["n"] * S * args.steps * world / (main_res["t_e2e_ms"] / 1e3)
+    launches_per_frame = S if args.pipeline == "fused" else 3 * S
+    line = {
+        "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n_particles": main_res["n"], "n_grid": main_res["n_grid"],
+                   "substeps_per_step": S, "pipeline": args.pipeline, "parallelism": "replicas%d" % world,
+                   "l2": "flushed between timed steps (256 MB write)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "particle-steps/s", "h2d_bytes_per_step": main_res["h2d"],
+                "d2h_bytes_per_step": main_res["d2h"]},
+        "gpu_launches": launches_per_frame * args.steps,
+        "clocks": main_res["clocks"],
+        "secondary": second,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * mpm.h -- C ABI of the GB300 MLS-MPM soft-tissue simulator.
+ *
+ * One handle owns one simulated scene: a set of Lagrangian particles of one
+ * Neo-Hookean material on a fixed Eulerian grid covering the unit cube
+ * [0,1)^3 (Sec. III-B: particles carry x, v, C, F; the grid carries mass and
+ * momentum), plus up to MPM_MAX_TOOLS rigid collision shapes (Sec. III-C).
+ * A sub-step is the paper's P2G (Eqs. 1-3, stress of Eqs. 5-6), grid
+ * operation (Eq. 7, gravity, tool contact Eqs. 11-19, walls) and G2P with
+ * advection (Eqs. 4, 8-10).  All numerical work runs in CUDA kernels for
+ * sm_103a; this header exposes plain pointers and sizes only.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an mpm_status.  On failure a description of the
+ *     last error on the calling thread is available from mpm_last_error().
+ *   - Device-side problems (non-finite values, inverted particles, particles
+ *     leaving the grid, capacity overruns) set a sticky error word on the
+ *     device.  Calls that synchronise (mpm_read_particles, mpm_synchronize,
+ *     the introspection calls) report it; mpm_step reports it as soon as an
+ *     earlier step that raised it has completed.  mpm_clear_error resets it.
+ *   - Work is issued on the CUDA stream given at creation (or by
+ *     mpm_set_stream) and is ordered with other work on that stream.
+ *   - Layouts: positions and velocities are n x 3 row-major float arrays;
+ *     F and C are n x 9 row-major (F[p*9 + 3*a + b] = F_ab of particle p).
+ *     Particle p of every output is the particle loaded at index p.
+ *   - Grid nodes are indexed [i][j][k], k fastest, node (i,j,k) at world
+ *     position (i, j, k) * dx with dx = 1 / n_grid.
+ *   - Caller-owned input buffers are copied; the caller may reuse them when
+ *     the call returns.  The library owns every device buffer it allocates.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef GBMPM_MPM_H
+#define GBMPM_MPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpm_handle mpm_handle;
+
+typedef enum mpm_status {
+    MPM_OK = 0,
+    MPM_ERR_ARG = -1,       /* invalid argument (NULL, out of range, wrong size) */
+    MPM_ERR_ALLOC = -2,     /* device or host allocation failed */
+    MPM_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+    MPM_ERR_NUMERIC = -4,   /* NaN/Inf in the state, or det F <= 0 (clamped to 1e-6 in ln) */
+    MPM_ERR_DOMAIN = -5,    /* a particle's stencil left the grid (clamped to the grid) */
+    MPM_ERR_TIMEOUT = -6,   /* a bounded device wait gave up */
+    MPM_ERR_STATE = -7,     /* call not valid in the handle's current state */
+    MPM_ERR_CAPACITY = -8,  /* an internal capacity was exceeded (see mpm_step) */
+    MPM_ERR_CFL = -9        /* a particle moved more than one 4-cell block in a sub-step */
+} mpm_status;
+
+enum {
+    MPM_MAX_TOOLS = 8,
+    MPM_PIPELINE_FUSED = 0, /* block-sorted particles; one fused kernel per sub-step */
+    MPM_PIPELINE_SPLIT = 1  /* unsorted particles; P2G, grid and G2P as separate kernels */
+};
+
+/* Tool shape kinds, shape[0] of mpm_set_tool_pose. */
+enum { MPM_TOOL_NONE = -1, MPM_TOOL_CAPSULE = 0, MPM_TOOL_BOX = 1 };
+
+typedef struct mpm_config {
+    int32_t n_grid;         /* nodes per axis: a power of two in [8, 512]; dx = 1/n_grid */
+    int32_t bound;          /* sticky wall band in nodes, >= 0 (walls zero every velocity
+                               component at nodes with an index < bound or >= n_grid - bound) */
+    float dt;               /* sub-step Delta t in seconds, > 0 */
+    float gravity[3];       /* m/s^2, added to grid velocities after Eq. 7 */
+    float E;                /* Young's modulus (Pa), >= 0 */
+    float nu;               /* Poisson's ratio, in [0, 0.5) */
+    float rho;              /* density (kg/m^3), > 0; particle mass = rho * particle volume */
+    float theta;            /* contact threshold: a node collides if its distance < theta */
+    float friction_mu;      /* Coulomb coefficient of Eq. 18, >= 0 */
+    int32_t pipeline;       /* MPM_PIPELINE_FUSED or MPM_PIPELINE_SPLIT */
+    int64_t max_particles;  /* capacity of the handle, >= 1 */
+} mpm_config;
+
+/* Optional device allocator.  alloc returns a device pointer of at least
+ * `bytes` bytes, 256-byte aligned, usable on `stream`, or NULL on failure;
+ * free releases it.  With alloc == NULL the library uses cudaMalloc/cudaFree. */
+typedef void *(*mpm_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*mpm_free_fn)(void *ptr, void *stream, void *ctx);
+
+/* Create a handle for the current CUDA device.  cuda_stream: a cudaStream_t
+ * (NULL = the legacy default stream).  Allocates every buffer sized by
+ * cfg->max_particles and cfg->n_grid up front.  *out receives the handle. */
+mpm_status mpm_create(const mpm_config *cfg, void *cuda_stream, mpm_alloc_fn alloc,
+                      mpm_free_fn free_fn, void *ctx, mpm_handle **out);
+
+/* Release every resource of the handle (waits for its stream first). */
+mpm_status mpm_destroy(mpm_handle *h);
+
+/* Replace the particle state with n particles (0 <= n <= max_particles).
+ * x: n x 3 positions (required); v: n x 3 or NULL (zero); F: n x 9 or NULL
+ * (identity); C: n x 9 or NULL (zero).  particle_volume: V_p^0 (> 0), the
+ * same for every particle (Table I).  on_device != 0: the pointers are device
+ * memory readable on the handle's stream; otherwise host memory.  The stored
+ * F is taken as already updated by Eq. 4, so the first P2G uses P(F) F^T of
+ * the given F (Eq. 3).  Asynchronous for device inputs. */
+mpm_status mpm_load_particles(mpm_handle *h, int64_t n, const float *x, const float *v,
+                              const float *F, const float *C, float particle_volume,
+                              int on_device);
+
+/* Set rigid tool tool_id (0 <= tool_id < MPM_MAX_TOOLS) (Sec. III-C).
+ * pose: world translation T (3) then rotation vector (3): a reference-frame
+ * point p sits at R p + T, R = exp([r]_x); grid nodes are mapped to the tool
+ * frame by Eq. 11.  shape: 8 floats, shape[0] = kind; capsule: shape[1] =
+ * radius, shape[2] = half-length of the axis segment along local y; box:
+ * shape[1..3] = half extents; kind MPM_TOOL_NONE removes the tool.  The pose
+ * is the target for the end of the next mpm_step call: during that call the
+ * tool moves uniformly (constant linear and angular velocity) from its
+ * current pose to the target, and that rigid velocity is v_co of Eq. 15.
+ * The first call for a tool places it without motion.  The pose is double
+ * precision because the tool velocity is a difference of nearby poses.
+ * Host arrays. */
+mpm_status mpm_set_tool_pose(mpm_handle *h, int32_t tool_id, const double pose[6],
+                             const float shape[8]);
+
+/* Advance n_substeps >= 0 sub-steps (P2G, grid operation, G2P; Sec. III-B).
+ * Asynchronous on the handle's stream.  The fused pipeline folds a stable
+ * counting sort of the particles by 4x4x4-cell grid block into each sub-step;
+ * a block may receive particles from at most 512 source chunks of 256
+ * particles per sub-step (MPM_ERR_CAPACITY otherwise). */
+mpm_status mpm_step(mpm_handle *h, int32_t n_substeps);
+
+/* Copy the particle state out in load order (n = the loaded count).  Any of
+ * x (n x 3), v (n x 3), F (n x 9), C (n x 9) may be NULL to skip it.
+ * on_device != 0: device pointers; otherwise host pointers.  Synchronises
+ * the stream and returns the sticky device status. */
+mpm_status mpm_read_particles(mpm_handle *h, float *x, float *v, float *F, float *C,
+                              int on_device);
+
+/* Thread-local description of the last failing call on this thread. */
+const char *mpm_last_error(void);
+
+/* ---------------------------------------------------------- introspection */
+
+/* Number of loaded particles. */
+mpm_status mpm_num_particles(mpm_handle *h, int64_t *n);
+
+/* Sub-steps taken since the last load. */
+mpm_status mpm_substeps_taken(mpm_handle *h, int64_t *count);
+
+/* Wait for the handle's stream and return the sticky device status. */
+mpm_status mpm_synchronize(mpm_handle *h);
+
+/* Reset the sticky device error word. */
+mpm_status mpm_clear_error(mpm_handle *h);
+
+/* Use another stream for subsequent work (the caller orders the switch). */
+mpm_status mpm_set_stream(mpm_handle *h, void *cuda_stream);
+
+/* Grid mass and momentum that the next sub-step's grid operation starts from
+ * (the P2G of the current particle state, Eqs. 1-2): n_grid^3 x 4 floats
+ * (m, mv_x, mv_y, mv_z) per node.  Synchronises. */
+mpm_status mpm_read_grid(mpm_handle *h, float *grid, int on_device);
+
+/* Grid velocities after the grid operation (Eq. 7, gravity, tools, walls)
+ * applied to mpm_read_grid's state with the tool poses a following
+ * mpm_step(h, 1) would use: n_grid^3 x 3 floats.  Synchronises. */
+mpm_status mpm_grid_velocity(mpm_handle *h, float *v, int on_device);
+
+/* Fused pipeline only: the current order of the particles, i.e. the result
+ * of the per-sub-step stable counting sort.  ids: n particle indices (load
+ * order) sorted by grid-block key, ties in the order of the previous sort
+ * (after a load: by particle index); keys: the block key of each entry,
+ * bx + nb*(by + nb*bz) with nb = n_grid/4 and b = floor(x/dx - 0.5)/4
+ * (clamped to the grid).  Host arrays of n entries.  Synchronises. */
+mpm_status mpm_read_order(mpm_handle *h, uint32_t *ids, uint32_t *keys);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBMPM_MPM_H */

@@ -27,13 +27,20 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle shared library if it is missing or stale."""
+    import fcntl
     os.makedirs(_BUILD, exist_ok=True)
+    with open(os.path.join(_BUILD, ".lock"), "w") as fh:
+        fcntl.flock(fh, fcntl.LOCK_EX)
+        _build_locked(force)
+    return _LIB
+
+
+def _build_locked(force):
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
                                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
-    return _LIB
 
 
 class Params(ct.Structure):

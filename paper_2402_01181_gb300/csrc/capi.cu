@@ -1,0 +1,705 @@
+// capi.cu -- host runtime behind the C ABI of include/mpm.h: device buffers,
+// particle load (with the stable block sort of the fused pipeline), tool pose
+// streams, CUDA-graph replay of sub-step sequences, readout and inspection.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/mpm.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace gbmpm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mpm_status fail(mpm_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CK(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(MPM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kMaxSubChunk = 512;   // sub-steps per captured graph / tool table
+
+// ------------------------------------------------------------ rotations
+
+struct Quat {
+    double w, x, y, z;
+};
+Quat qmul(const Quat &a, const Quat &b) {
+    return {a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z, a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
+            a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x, a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
+}
+Quat qexp_rotvec(const double r[3]) {
+    const double th = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    if (th < 1e-12) {
+        Quat q{1.0, 0.5 * r[0], 0.5 * r[1], 0.5 * r[2]};
+        const double nq = std::sqrt(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
+        return {q.w / nq, q.x / nq, q.y / nq, q.z / nq};
+    }
+    const double s = std::sin(0.5 * th) / th;
+    return {std::cos(0.5 * th), s * r[0], s * r[1], s * r[2]};
+}
+void qlog_rotvec(Quat q, double r[3]) {   // shortest rotation
+    if (q.w < 0) { q.w = -q.w; q.x = -q.x; q.y = -q.y; q.z = -q.z; }
+    const double v = std::sqrt(q.x * q.x + q.y * q.y + q.z * q.z);
+    if (v < 1e-12) { r[0] = 2 * q.x; r[1] = 2 * q.y; r[2] = 2 * q.z; return; }
+    const double th = 2.0 * std::atan2(v, q.w);
+    r[0] = th * q.x / v; r[1] = th * q.y / v; r[2] = th * q.z / v;
+}
+void qmatrix(const Quat &q, double R[9]) {
+    const double w = q.w, x = q.x, y = q.y, z = q.z;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
+}
+
+struct HostTool {
+    int kind = MPM_TOOL_NONE;
+    double dims[3] = {0, 0, 0};
+    double cur[6] = {0, 0, 0, 0, 0, 0};   // pose at the end of the last sub-step taken
+    double tgt[6] = {0, 0, 0, 0, 0, 0};   // pose at the end of the next call
+};
+
+struct Alloc {
+    void *p;
+    size_t bytes;
+};
+
+}  // namespace
+
+struct mpm_handle {
+    mpm_config cfg{};
+    DevParams P{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    mpm_alloc_fn alloc_fn = nullptr;
+    mpm_free_fn free_fn = nullptr;
+    void *alloc_ctx = nullptr;
+    std::vector<Alloc> allocs;
+    int device = 0, num_sms = 0, fused_grid = 0, elem_grid = 0;
+    uint32_t nblocks = 0, chunk_cap = 0;
+    int64_t n = 0;
+    bool loaded = false;
+    uint32_t step = 0;          // fused: device sub-step index mirrored on the host
+    int64_t taken = 0;
+    float particle_volume = 0.f;
+    // buffers
+    FusedBufs fb{};
+    SortScratch sort{};
+    float *staging = nullptr;   // 24 floats per particle (AoS x, v, F, C)
+    float4 *dense = nullptr;    // n^3 float4, allocated on first inspection
+    ToolFrame *d_frames = nullptr;
+    ToolFrame *h_frames = nullptr;   // pinned
+    uint32_t *h_err = nullptr;       // pinned copy of Ctrl::err
+    cudaEvent_t ev_err = nullptr, ev_frames = nullptr;
+    bool err_pending = false;
+    HostTool tools[MPM_MAX_TOOLS];
+    std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+    bool use_graphs = true;
+};
+
+namespace {
+
+mpm_status dalloc(mpm_handle *h, void **out, size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (h->alloc_fn) {
+        p = h->alloc_fn(bytes, (void *)h->stream, h->alloc_ctx);
+        if (!p) return fail(MPM_ERR_ALLOC, "allocator callback returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) return fail(MPM_ERR_ALLOC, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    h->allocs.push_back({p, bytes});
+    *out = p;
+    return MPM_OK;
+}
+
+template <typename T>
+mpm_status dalloc_t(mpm_handle *h, T **out, size_t count) {
+    void *p = nullptr;
+    mpm_status st = dalloc(h, &p, count * sizeof(T));
+    *out = static_cast<T *>(p);
+    return st;
+}
+
+void release_all(mpm_handle *h) {
+    cudaStreamSynchronize(h->stream);
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.second);
+    h->graphs.clear();
+    for (auto &a : h->allocs) {
+        if (h->alloc_fn) {
+            if (h->free_fn) h->free_fn(a.p, (void *)h->stream, h->alloc_ctx);
+        } else {
+            cudaFree(a.p);
+        }
+    }
+    h->allocs.clear();
+    if (h->h_frames) cudaFreeHost(h->h_frames);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->ev_err) cudaEventDestroy(h->ev_err);
+    if (h->ev_frames) cudaEventDestroy(h->ev_frames);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    h->h_frames = nullptr;
+    h->h_err = nullptr;
+}
+
+mpm_status status_of(uint32_t err) {
+    if (err & kErrNumeric) return fail(MPM_ERR_NUMERIC, "device: non-finite state or det F <= 0");
+    if (err & kErrDomain) return fail(MPM_ERR_DOMAIN, "device: a particle stencil left the grid (clamped)");
+    if (err & kErrCfl) return fail(MPM_ERR_CFL, "device: a particle moved more than one block in a sub-step");
+    if (err & kErrCapacity) return fail(MPM_ERR_CAPACITY, "device: run-table or particle-count capacity exceeded");
+    return MPM_OK;
+}
+
+bool is_fused(const mpm_handle *h) { return h->cfg.pipeline == MPM_PIPELINE_FUSED; }
+
+// Device sub-step index for buffer selection.
+int cur_par(const mpm_handle *h) { return (int)(h->step & 1u); }
+int cur_m3(const mpm_handle *h) { return (int)(h->step % 3u); }
+
+const PState &cur_state(const mpm_handle *h) { return is_fused(h) ? h->fb.P[cur_par(h)] : h->fb.P[0]; }
+
+// Tool frames of nsub sub-steps of a call that moves every tool from its
+// current pose to its target uniformly over `total` sub-steps, starting at
+// sub-step `first` of the call.
+int fill_frames(mpm_handle *h, int first, int nsub, int total, ToolFrame *out) {
+    int ntools = 0;
+    for (int t = 0; t < MPM_MAX_TOOLS; ++t)
+        if (h->tools[t].kind != MPM_TOOL_NONE) ntools = t + 1;
+    const double span = (double)total * (double)h->cfg.dt;
+    for (int t = 0; t < ntools; ++t) {
+        const HostTool &tl = h->tools[t];
+        const Quat q0 = qexp_rotvec(tl.cur + 3), q1 = qexp_rotvec(tl.tgt + 3);
+        const Quat dq = qmul(q1, Quat{q0.w, -q0.x, -q0.y, -q0.z});
+        double phi[3];
+        qlog_rotvec(dq, phi);
+        double reach = tl.kind == MPM_TOOL_CAPSULE ? tl.dims[0] + tl.dims[1]
+                                                   : std::sqrt(tl.dims[0] * tl.dims[0] + tl.dims[1] * tl.dims[1] +
+                                                               tl.dims[2] * tl.dims[2]);
+        reach += std::max(0.0, (double)h->cfg.theta);
+        reach = reach * 1.001 + 1e-6;
+        for (int k = 0; k < nsub; ++k) {
+            const double s = (double)(first + k + 1) / (double)total;
+            ToolFrame &f = out[k * MPM_MAX_TOOLS + t];
+            std::memset(&f, 0, sizeof f);
+            f.kind = tl.kind;
+            if (tl.kind == MPM_TOOL_NONE) continue;
+            const double rs[3] = {s * phi[0], s * phi[1], s * phi[2]};
+            double R[9];
+            qmatrix(qmul(qexp_rotvec(rs), q0), R);
+            for (int i = 0; i < 9; ++i) f.R[i] = (float)R[i];
+            for (int a = 0; a < 3; ++a) {
+                f.T[a] = (float)(tl.cur[a] + s * (tl.tgt[a] - tl.cur[a]));
+                f.u[a] = (float)((tl.tgt[a] - tl.cur[a]) / span);
+                f.w[a] = (float)(phi[a] / span);
+                f.dims[a] = (float)tl.dims[a];
+            }
+            f.reach2 = (float)(reach * reach);
+        }
+    }
+    return ntools;
+}
+
+// Upload frames for sub-steps [first, first+nsub) of a call of `total`.
+mpm_status upload_frames(mpm_handle *h, int first, int nsub, int total) {
+    // the pinned staging buffer may still feed an earlier copy
+    CK(cudaEventSynchronize(h->ev_frames));
+    const int ntools = fill_frames(h, first, nsub, total, h->h_frames);
+    h->P.ntools = ntools;
+    if (ntools > 0)
+        CK(cudaMemcpyAsync(h->d_frames, h->h_frames, sizeof(ToolFrame) * MPM_MAX_TOOLS * nsub, cudaMemcpyHostToDevice,
+                           h->stream));
+    CK(cudaEventRecord(h->ev_frames, h->stream));
+    return MPM_OK;
+}
+
+mpm_status poll_error(mpm_handle *h, bool wait) {
+    if (!h->err_pending) return MPM_OK;
+    if (wait) {
+        CK(cudaEventSynchronize(h->ev_err));
+    } else {
+        cudaError_t q = cudaEventQuery(h->ev_err);
+        if (q == cudaErrorNotReady) return MPM_OK;
+        if (q != cudaSuccess) return fail(MPM_ERR_CUDA, "cudaEventQuery: %s", cudaGetErrorString(q));
+    }
+    return status_of(*h->h_err);
+}
+
+mpm_status enqueue_error_copy(mpm_handle *h) {
+    CK(cudaMemcpyAsync(h->h_err, &h->fb.ctrl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaEventRecord(h->ev_err, h->stream));
+    h->err_pending = true;
+    return MPM_OK;
+}
+
+// Issue nsub sub-steps on stream st (used directly and under capture).
+mpm_status issue_substeps(mpm_handle *h, int nsub, bool write_vc_last, cudaStream_t st, int ntools) {
+    DevParams P = h->P;
+    P.ntools = ntools;
+    const uint32_t n = (uint32_t)h->n;
+    for (int k = 0; k < nsub; ++k) {
+        const ToolFrame *fr = h->d_frames + (size_t)k * MPM_MAX_TOOLS;
+        const bool vc = write_vc_last && k == nsub - 1;
+        if (is_fused(h)) {
+            launch_fused_step(P, h->fb, fr, vc, h->fused_grid, st);
+        } else {
+            CK(cudaMemsetAsync(h->fb.G[0], 0, sizeof(float4) * (size_t)h->P.n * h->P.n * h->P.n, st));
+            launch_p2g_scatter(P, h->fb.P[0], h->fb.vc, n, h->fb.G[0], h->fb.ctrl, h->elem_grid, st);
+            launch_grid_update_dense(P, h->fb.G[0], fr, h->elem_grid, st);
+            launch_g2p_split(P, h->fb.P[0], h->fb.vc, n, h->fb.G[0], h->fb.ctrl, h->elem_grid, st);
+        }
+    }
+    CK(cudaGetLastError());
+    return MPM_OK;
+}
+
+mpm_status run_chunk(mpm_handle *h, int nsub, bool write_vc_last, int ntools) {
+    if (!h->use_graphs) return issue_substeps(h, nsub, write_vc_last, h->stream, ntools);
+    // graphs are keyed by length, the vc flag and the number of tool slots
+    const std::pair<int, int> key(nsub, (write_vc_last ? 1 : 0) | (ntools << 1));
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        mpm_status st = issue_substeps(h, nsub, write_vc_last, h->cap_stream, ntools);
+        cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+        if (st != MPM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(MPM_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(MPM_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        it = h->graphs.emplace(key, ex).first;
+    }
+    CK(cudaGraphLaunch(it->second, h->stream));
+    return MPM_OK;
+}
+
+mpm_status check_handle(mpm_handle *h) {
+    if (!h) return fail(MPM_ERR_ARG, "NULL handle");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != h->device) CK(cudaSetDevice(h->device));
+    return MPM_OK;
+}
+
+}  // namespace
+
+// =================================================================== ABI
+
+extern "C" {
+
+const char *mpm_last_error(void) { return g_last_error.c_str(); }
+
+mpm_status mpm_create(const mpm_config *cfg, void *cuda_stream, mpm_alloc_fn alloc, mpm_free_fn free_fn, void *ctx,
+                      mpm_handle **out) {
+    if (!cfg || !out) return fail(MPM_ERR_ARG, "mpm_create: NULL config or output pointer");
+    *out = nullptr;
+    const int n = cfg->n_grid;
+    if (n < 8 || n > 512 || (n & (n - 1)) != 0) return fail(MPM_ERR_ARG, "n_grid must be a power of two in [8, 512]");
+    if (cfg->bound < 0 || 2 * cfg->bound >= n) return fail(MPM_ERR_ARG, "bound out of range");
+    if (!(cfg->dt > 0.f) || !std::isfinite(cfg->dt)) return fail(MPM_ERR_ARG, "dt must be positive");
+    if (!(cfg->E >= 0.f) || !(cfg->nu >= 0.f) || !(cfg->nu < 0.5f)) return fail(MPM_ERR_ARG, "need E >= 0, 0 <= nu < 0.5");
+    if (!(cfg->rho > 0.f)) return fail(MPM_ERR_ARG, "rho must be positive");
+    if (!(cfg->friction_mu >= 0.f)) return fail(MPM_ERR_ARG, "friction_mu must be >= 0");
+    if (!std::isfinite(cfg->theta) || !std::isfinite(cfg->gravity[0]) || !std::isfinite(cfg->gravity[1]) ||
+        !std::isfinite(cfg->gravity[2]))
+        return fail(MPM_ERR_ARG, "theta and gravity must be finite");
+    if (cfg->pipeline != MPM_PIPELINE_FUSED && cfg->pipeline != MPM_PIPELINE_SPLIT)
+        return fail(MPM_ERR_ARG, "unknown pipeline %d", cfg->pipeline);
+    if (cfg->max_particles < 1 || cfg->max_particles > (int64_t)1 << 30)
+        return fail(MPM_ERR_ARG, "max_particles must be in [1, 2^30]");
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(MPM_ERR_ARG, "alloc and free callbacks go together");
+
+    mpm_handle *h = new (std::nothrow) mpm_handle();
+    if (!h) return fail(MPM_ERR_ALLOC, "host allocation of the handle failed");
+    h->cfg = *cfg;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->alloc_fn = alloc;
+    h->free_fn = free_fn;
+    h->alloc_ctx = ctx;
+    const char *ng = getenv("GBMPM_NO_GRAPHS");
+    h->use_graphs = !(ng && ng[0] == '1');
+
+    auto bail = [&](mpm_status st) {
+        release_all(h);
+        delete h;
+        return st;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(fail(MPM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return bail(fail(MPM_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e)));
+
+    DevParams &P = h->P;
+    P.n = n;
+    P.nb = n / 4;
+    P.bound = cfg->bound;
+    P.ntools = 0;
+    P.dx = 1.0f / (float)n;
+    P.inv_dx = (float)n;
+    P.dt = cfg->dt;
+    P.gx = cfg->gravity[0];
+    P.gy = cfg->gravity[1];
+    P.gz = cfg->gravity[2];
+    P.mass = 0.f;
+    const double E = cfg->E, nu = cfg->nu;   // Eq. 6
+    P.mu = (float)(E / (2.0 * (1.0 + nu)));
+    P.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+    P.stress_k = 0.f;
+    P.theta = cfg->theta;
+    P.fric = cfg->friction_mu;
+
+    const size_t N = (size_t)cfg->max_particles;
+    const size_t nn = (size_t)n * n * n;
+    h->nblocks = (uint32_t)(P.nb * P.nb * P.nb);
+    h->chunk_cap = h->nblocks + (uint32_t)(N / kFusedThreads) + 1;
+    h->fb.nblocks = h->nblocks;
+    h->elem_grid = h->num_sms * 8;
+    const int occ = fused_step_occupancy(kFusedThreads);
+    h->fused_grid = h->num_sms * std::max(occ, 1);
+
+    mpm_status st;
+    const int nbuf = cfg->pipeline == MPM_PIPELINE_FUSED ? 2 : 1;
+    for (int b = 0; b < nbuf; ++b) {
+        if ((st = dalloc_t(h, &h->fb.P[b].xi, N)) != MPM_OK) return bail(st);
+        if ((st = dalloc_t(h, &h->fb.P[b].f0, N)) != MPM_OK) return bail(st);
+        if ((st = dalloc_t(h, &h->fb.P[b].f1, N)) != MPM_OK) return bail(st);
+        if ((st = dalloc_t(h, &h->fb.P[b].f2, N)) != MPM_OK) return bail(st);
+    }
+    if (nbuf == 1) h->fb.P[1] = h->fb.P[0];
+    if ((st = dalloc_t(h, &h->fb.vc.vc0, N)) != MPM_OK) return bail(st);
+    if ((st = dalloc_t(h, &h->fb.vc.vc1, N)) != MPM_OK) return bail(st);
+    if ((st = dalloc_t(h, &h->fb.vc.vc2, N)) != MPM_OK) return bail(st);
+    const int ngrid = cfg->pipeline == MPM_PIPELINE_FUSED ? 3 : 1;
+    for (int g = 0; g < ngrid; ++g)
+        if ((st = dalloc_t(h, &h->fb.G[g], nn)) != MPM_OK) return bail(st);
+    for (int g = ngrid; g < 3; ++g) h->fb.G[g] = h->fb.G[0];
+    if ((st = dalloc_t(h, &h->fb.ctrl, 1)) != MPM_OK) return bail(st);
+    if ((st = dalloc_t(h, &h->staging, 24 * N)) != MPM_OK) return bail(st);
+    if ((st = dalloc_t(h, &h->d_frames, (size_t)kMaxSubChunk * MPM_MAX_TOOLS)) != MPM_OK) return bail(st);
+    if (cfg->pipeline == MPM_PIPELINE_FUSED) {
+        for (int b = 0; b < 2; ++b) {
+            if ((st = dalloc_t(h, &h->fb.chunks[b], h->chunk_cap)) != MPM_OK) return bail(st);
+            if ((st = dalloc_t(h, &h->fb.tabs[b], h->nblocks)) != MPM_OK) return bail(st);
+            if ((st = dalloc_t(h, &h->fb.alist[b], h->nblocks)) != MPM_OK) return bail(st);
+        }
+        for (int b = 0; b < 3; ++b)
+            if ((st = dalloc_t(h, &h->fb.clist[b], h->nblocks)) != MPM_OK) return bail(st);
+        if ((st = dalloc_t(h, &h->fb.astamp, h->nblocks)) != MPM_OK) return bail(st);
+        if ((st = dalloc_t(h, &h->fb.gstamp, h->nblocks)) != MPM_OK) return bail(st);
+        if ((st = dalloc_t(h, &h->sort.keys, N)) != MPM_OK) return bail(st);
+        if ((st = dalloc_t(h, &h->sort.perm, N)) != MPM_OK) return bail(st);
+        if ((st = dalloc_t(h, &h->sort.counts, h->nblocks)) != MPM_OK) return bail(st);
+        if ((st = dalloc_t(h, &h->sort.offsets, h->nblocks + 1)) != MPM_OK) return bail(st);
+        if ((st = dalloc_t(h, &h->sort.cursor, h->nblocks)) != MPM_OK) return bail(st);
+    }
+    e = cudaMallocHost(&h->h_frames, sizeof(ToolFrame) * kMaxSubChunk * MPM_MAX_TOOLS);
+    if (e != cudaSuccess) return bail(fail(MPM_ERR_ALLOC, "cudaMallocHost: %s", cudaGetErrorString(e)));
+    e = cudaMallocHost(&h->h_err, sizeof(uint32_t));
+    if (e != cudaSuccess) return bail(fail(MPM_ERR_ALLOC, "cudaMallocHost: %s", cudaGetErrorString(e)));
+    *h->h_err = 0;
+    if ((e = cudaEventCreateWithFlags(&h->ev_err, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_frames, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(fail(MPM_ERR_CUDA, "event/stream creation: %s", cudaGetErrorString(e)));
+    e = cudaEventRecord(h->ev_frames, h->stream);
+    if (e == cudaSuccess && h->fb.astamp) e = cudaMemsetAsync(h->fb.astamp, 0, sizeof(uint32_t) * h->nblocks, h->stream);
+    if (e == cudaSuccess && h->fb.gstamp) e = cudaMemsetAsync(h->fb.gstamp, 0, sizeof(uint32_t) * h->nblocks, h->stream);
+    for (int b = 0; b < 2 && e == cudaSuccess && h->fb.tabs[b]; ++b)
+        e = cudaMemsetAsync(h->fb.tabs[b], 0, sizeof(BlockTab) * h->nblocks, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->fb.ctrl, 0, sizeof(Ctrl), h->stream);
+    if (e != cudaSuccess) return bail(fail(MPM_ERR_CUDA, "initial clears: %s", cudaGetErrorString(e)));
+    *out = h;
+    return MPM_OK;
+}
+
+mpm_status mpm_destroy(mpm_handle *h) {
+    if (!h) return fail(MPM_ERR_ARG, "NULL handle");
+    cudaSetDevice(h->device);
+    release_all(h);
+    delete h;
+    return MPM_OK;
+}
+
+mpm_status mpm_set_stream(mpm_handle *h, void *cuda_stream) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    h->stream = (cudaStream_t)cuda_stream;
+    CK(cudaEventRecord(h->ev_frames, h->stream));
+    return MPM_OK;
+}
+
+mpm_status mpm_load_particles(mpm_handle *h, int64_t n, const float *x, const float *v, const float *F, const float *C,
+                              float particle_volume, int on_device) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (n < 0 || n > h->cfg.max_particles) return fail(MPM_ERR_ARG, "n = %lld outside [0, max_particles]", (long long)n);
+    if (n > 0 && !x) return fail(MPM_ERR_ARG, "x is required");
+    if (!(particle_volume > 0.f) || !std::isfinite(particle_volume)) return fail(MPM_ERR_ARG, "particle_volume must be > 0");
+    const size_t N = (size_t)n;
+    // inputs in device memory (staging copies for host inputs)
+    const float *dx = x, *dv = v, *dF = F, *dC = C;
+    if (!on_device && n > 0) {
+        float *sx = h->staging, *sv = sx + 3 * N, *sF = sv + 3 * N, *sC = sF + 9 * N;
+        CK(cudaMemcpyAsync(sx, x, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->stream));
+        dx = sx;
+        if (v) { CK(cudaMemcpyAsync(sv, v, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->stream)); dv = sv; }
+        if (F) { CK(cudaMemcpyAsync(sF, F, sizeof(float) * 9 * N, cudaMemcpyHostToDevice, h->stream)); dF = sF; }
+        if (C) { CK(cudaMemcpyAsync(sC, C, sizeof(float) * 9 * N, cudaMemcpyHostToDevice, h->stream)); dC = sC; }
+    }
+    h->particle_volume = particle_volume;
+    h->P.mass = h->cfg.rho * particle_volume;
+    h->P.stress_k = (float)((double)h->cfg.dt * particle_volume * 4.0 * (double)h->P.inv_dx * h->P.inv_dx);
+    // graphs captured the old parameters
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.second);
+    h->graphs.clear();
+
+    Ctrl c{};
+    const uint32_t k0 = h->step + 2;   // fresh stamps: every table entry from before is older
+    c.step = k0;
+    c.n_particles = (uint32_t)n;
+    CK(cudaMemcpyAsync(h->fb.ctrl, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));   // the host Ctrl and input buffers must outlive the copies
+    h->step = k0;
+    h->n = n;
+    h->taken = 0;
+    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+    if (is_fused(h)) {
+        for (int g = 0; g < 3; ++g) CK(cudaMemsetAsync(h->fb.G[g], 0, sizeof(float4) * nn, h->stream));
+        CK(cudaMemsetAsync(h->sort.counts, 0, sizeof(uint32_t) * h->nblocks, h->stream));
+        launch_block_sort(h->P, dx, (uint32_t)n, h->sort, h->fb.ctrl, h->elem_grid, h->stream);
+        const int par = cur_par(h);
+        launch_place_sorted(h->P, dx, dv, dF, dC, (uint32_t)n, h->sort, h->fb.P[par], h->fb.vc, h->elem_grid, h->stream);
+        launch_init_tables(h->P, h->sort, h->fb, k0, h->elem_grid, h->stream);
+        launch_p2g_scatter(h->P, h->fb.P[par], h->fb.vc, (uint32_t)n, h->fb.G[cur_m3(h)], h->fb.ctrl, h->elem_grid,
+                           h->stream);
+    } else {
+        launch_load_identity(dx, dv, dF, dC, (uint32_t)n, h->fb.P[0], h->fb.vc, h->fb.ctrl, h->elem_grid, h->stream);
+    }
+    CK(cudaGetLastError());
+    h->loaded = true;
+    if (!on_device) CK(cudaStreamSynchronize(h->stream));
+    return enqueue_error_copy(h);
+}
+
+mpm_status mpm_set_tool_pose(mpm_handle *h, int32_t tool_id, const double pose[6], const float shape[8]) {
+    if (!h) return fail(MPM_ERR_ARG, "NULL handle");
+    if (tool_id < 0 || tool_id >= MPM_MAX_TOOLS) return fail(MPM_ERR_ARG, "tool_id %d out of range", tool_id);
+    if (!pose || !shape) return fail(MPM_ERR_ARG, "NULL pose or shape");
+    HostTool &t = h->tools[tool_id];
+    const int kind = (int)shape[0];
+    if (kind == MPM_TOOL_NONE) {
+        t = HostTool();
+        return MPM_OK;
+    }
+    if (kind != MPM_TOOL_CAPSULE && kind != MPM_TOOL_BOX) return fail(MPM_ERR_ARG, "unknown tool kind %d", kind);
+    for (int i = 0; i < 6; ++i)
+        if (!std::isfinite(pose[i])) return fail(MPM_ERR_ARG, "non-finite pose");
+    for (int i = 1; i < 4; ++i)
+        if (!(shape[i] >= 0.f) || !std::isfinite(shape[i])) return fail(MPM_ERR_ARG, "shape sizes must be finite and >= 0");
+    const bool fresh = t.kind == MPM_TOOL_NONE;
+    t.kind = kind;
+    for (int a = 0; a < 3; ++a) t.dims[a] = shape[1 + a];
+    for (int i = 0; i < 6; ++i) {
+        t.tgt[i] = pose[i];
+        if (fresh) t.cur[i] = pose[i];
+    }
+    return MPM_OK;
+}
+
+mpm_status mpm_step(mpm_handle *h, int32_t n_substeps) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (n_substeps < 0) return fail(MPM_ERR_ARG, "n_substeps must be >= 0");
+    if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
+    if ((st = poll_error(h, false)) != MPM_OK) return st;
+    if (n_substeps == 0) return MPM_OK;
+    if (h->n == 0) {
+        for (auto &t : h->tools) std::memcpy(t.cur, t.tgt, sizeof t.cur);
+        return MPM_OK;
+    }
+    for (int first = 0; first < n_substeps; first += kMaxSubChunk) {
+        const int m = std::min(kMaxSubChunk, n_substeps - first);
+        if ((st = upload_frames(h, first, m, n_substeps)) != MPM_OK) return st;
+        const bool last = first + m == n_substeps;
+        if ((st = run_chunk(h, m, last, h->P.ntools)) != MPM_OK) return st;
+        if (is_fused(h)) h->step += (uint32_t)m;
+    }
+    h->taken += n_substeps;
+    for (auto &t : h->tools) std::memcpy(t.cur, t.tgt, sizeof t.cur);
+    return enqueue_error_copy(h);
+}
+
+mpm_status mpm_synchronize(mpm_handle *h) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    uint32_t err = 0;
+    CK(cudaMemcpy(&err, &h->fb.ctrl->err, sizeof err, cudaMemcpyDeviceToHost));
+    return status_of(err);
+}
+
+mpm_status mpm_clear_error(mpm_handle *h) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    CK(cudaMemsetAsync(&h->fb.ctrl->err, 0, sizeof(uint32_t), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *h->h_err = 0;
+    h->err_pending = false;
+    return MPM_OK;
+}
+
+mpm_status mpm_num_particles(mpm_handle *h, int64_t *n) {
+    if (!h || !n) return fail(MPM_ERR_ARG, "NULL argument");
+    *n = h->n;
+    return MPM_OK;
+}
+
+mpm_status mpm_substeps_taken(mpm_handle *h, int64_t *count) {
+    if (!h || !count) return fail(MPM_ERR_ARG, "NULL argument");
+    *count = h->taken;
+    return MPM_OK;
+}
+
+mpm_status mpm_read_particles(mpm_handle *h, float *x, float *v, float *F, float *C, int on_device) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
+    const size_t N = (size_t)h->n;
+    if (N > 0) {
+        if (on_device) {
+            launch_read_out(cur_state(h), h->fb.vc, (uint32_t)N, x, v, F, C, h->elem_grid, h->stream);
+        } else {
+            float *sx = h->staging, *sv = sx + 3 * N, *sF = sv + 3 * N, *sC = sF + 9 * N;
+            launch_read_out(cur_state(h), h->fb.vc, (uint32_t)N, x ? sx : nullptr, v ? sv : nullptr,
+                            F ? sF : nullptr, C ? sC : nullptr, h->elem_grid, h->stream);
+            if (x) CK(cudaMemcpyAsync(x, sx, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
+            if (v) CK(cudaMemcpyAsync(v, sv, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
+            if (F) CK(cudaMemcpyAsync(F, sF, sizeof(float) * 9 * N, cudaMemcpyDeviceToHost, h->stream));
+            if (C) CK(cudaMemcpyAsync(C, sC, sizeof(float) * 9 * N, cudaMemcpyDeviceToHost, h->stream));
+        }
+        CK(cudaGetLastError());
+    }
+    return mpm_synchronize(h);
+}
+
+static mpm_status ensure_dense(mpm_handle *h) {
+    if (h->dense) return MPM_OK;
+    return dalloc_t(h, &h->dense, (size_t)h->P.n * h->P.n * h->P.n);
+}
+
+// The grid the next sub-step starts from: fused pipelines keep it in
+// G[step % 3]; the split pipeline recomputes it into G[0].
+static const float4 *current_grid(mpm_handle *h) {
+    if (is_fused(h)) return h->fb.G[cur_m3(h)];
+    cudaMemsetAsync(h->fb.G[0], 0, sizeof(float4) * (size_t)h->P.n * h->P.n * h->P.n, h->stream);
+    launch_p2g_scatter(h->P, h->fb.P[0], h->fb.vc, (uint32_t)h->n, h->fb.G[0], h->fb.ctrl, h->elem_grid, h->stream);
+    return h->fb.G[0];
+}
+
+mpm_status mpm_read_grid(mpm_handle *h, float *grid, int on_device) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (!grid) return fail(MPM_ERR_ARG, "NULL output");
+    if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
+    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+    const float4 *G = current_grid(h);
+    if (on_device) {
+        launch_grid_to_dense(h->P.n, h->P.nb, G, (float4 *)grid, h->elem_grid, h->stream);
+    } else {
+        if ((st = ensure_dense(h)) != MPM_OK) return st;
+        launch_grid_to_dense(h->P.n, h->P.nb, G, h->dense, h->elem_grid, h->stream);
+        CK(cudaMemcpyAsync(grid, h->dense, sizeof(float4) * nn, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaGetLastError());
+    return mpm_synchronize(h);
+}
+
+mpm_status mpm_grid_velocity(mpm_handle *h, float *v, int on_device) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (!v) return fail(MPM_ERR_ARG, "NULL output");
+    if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
+    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+    if ((st = upload_frames(h, 0, 1, 1)) != MPM_OK) return st;
+    const float4 *G = current_grid(h);
+    float *outp = v;
+    if (!on_device) {
+        if ((st = ensure_dense(h)) != MPM_OK) return st;
+        outp = reinterpret_cast<float *>(h->dense);
+    }
+    launch_grid_velocity_dense(h->P, G, h->d_frames, outp, h->elem_grid, h->stream);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(v, outp, sizeof(float) * 3 * nn, cudaMemcpyDeviceToHost, h->stream));
+    return mpm_synchronize(h);
+}
+
+mpm_status mpm_read_order(mpm_handle *h, uint32_t *ids, uint32_t *keys) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (!is_fused(h)) return fail(MPM_ERR_STATE, "the split pipeline keeps particles unsorted");
+    if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
+    if (h->n > 0 && (!ids || !keys)) return fail(MPM_ERR_ARG, "NULL output");
+    CK(cudaStreamSynchronize(h->stream));
+    const int par = cur_par(h);
+    const uint32_t nb = (uint32_t)h->P.nb;
+    std::vector<BlockTab> tabs(h->nblocks);
+    std::vector<Chunk> chunks(h->chunk_cap);
+    std::vector<float4> xi((size_t)h->n);
+    CK(cudaMemcpy(tabs.data(), h->fb.tabs[par], sizeof(BlockTab) * h->nblocks, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(chunks.data(), h->fb.chunks[par], sizeof(Chunk) * h->chunk_cap, cudaMemcpyDeviceToHost));
+    if (h->n > 0) CK(cudaMemcpy(xi.data(), h->fb.P[par].xi, sizeof(float4) * h->n, cudaMemcpyDeviceToHost));
+    size_t w = 0;
+    for (uint32_t b = 0; b < h->nblocks; ++b) {
+        const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+        for (int d = 26; d >= 0; --d) {
+            const int sx = bx - (d % 3 - 1), sy = by - ((d / 3) % 3 - 1), sz = bz - (d / 9 - 1);
+            if (sx < 0 || sy < 0 || sz < 0 || sx >= (int)nb || sy >= (int)nb || sz >= (int)nb) continue;
+            const BlockTab &t = tabs[block_id(sx, sy, sz, nb)];
+            if (t.stamp != h->step) continue;
+            for (uint32_t p = 0; p < t.npass; ++p) {
+                if (t.first + p >= h->chunk_cap) return fail(MPM_ERR_STATE, "corrupt run table");
+                const uint2 r = chunks[t.first + p].run[d];
+                for (uint32_t q = 0; q < r.y; ++q) {
+                    if (w >= (size_t)h->n || r.x + q >= (size_t)h->n) return fail(MPM_ERR_STATE, "corrupt run table");
+                    uint32_t id;
+                    std::memcpy(&id, &xi[r.x + q].w, sizeof id);
+                    ids[w] = id;
+                    keys[w] = b;
+                    ++w;
+                }
+            }
+        }
+    }
+    if (w != (size_t)h->n) return fail(MPM_ERR_STATE, "run tables list %zu of %lld particles", w, (long long)h->n);
+    return mpm_synchronize(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,432 @@
+// kernel_fused.cu -- one MLS-MPM sub-step as a single persistent kernel over
+// the occupied 4x4x4-cell grid blocks.
+//
+// Sub-step k reads the grid G_k (mass, momentum after P2G of the particles at
+// x_k) and the particles, grouped by the block of their stencil base, and
+// writes x_{k+1}, F_{k+1} and the P2G of the new state into G_{k+1}:
+//
+//   per occupied block b (one CTA iteration):
+//   1. grid operation (Eq. 7, gravity, tool contact Eqs. 11, 15-19, walls) of
+//      the 6^3 nodes that the stencils of b's particles touch, into shared
+//      memory;
+//   2. per particle: G2P (Eqs. 8-9), F update (Eq. 4), advection (Eq. 10),
+//      Kirchhoff stress of the new F (Eqs. 5-6) and the affine momentum
+//      A = m C - dt V^0 (4/dx^2) tau, then P2G (Eqs. 1-3) of the new state
+//      into an 8^3-node shared-memory arena around b (global atomics for a
+//      particle that moved further than one cell);
+//   3. a stable counting sort of the particles by their new block: every
+//      256-particle pass writes its particles grouped by the direction
+//      (-1..1)^3 to their new block, and records where each group starts;
+//      the next sub-step's CTA for block b' reads the runs heading to b' from
+//      its 27 neighbours, in ascending source-block order;
+//   4. the arena is added to G_{k+1} with float4 atomics.
+//
+// Grid buffers rotate over three slots (read G_k, write G_{k+1}, clear
+// G_{k-1} for reuse), particle buffers and run tables over two; the last CTA
+// to finish resets the per-launch counters and advances the sub-step index.
+#include "common.cuh"
+#include "launch.h"
+
+namespace gbmpm {
+
+namespace {
+
+constexpr int T = kFusedThreads;
+constexpr int NW = T / 32;
+constexpr int CMAX = 512;   // run candidates (source chunk x direction) per block
+
+struct FusedSmem {
+    float4 v[216];               // grid velocities of nodes [4b, 4b+5]^3
+    float acc[4][512];           // P2G arena over nodes [4b-1, 4b+6]^3: m, mv_x, mv_y, mv_z
+    ToolFrame tools[kMaxTools];
+    uint32_t cand_start[CMAX];   // first slot of each run
+    uint32_t cand_pre[CMAX + 1]; // exclusive prefix of run lengths
+    uint32_t lane_first[27], lane_np[27], lane_off[27];
+    uint32_t wcnt[2][NW][28];    // per pass parity: per-warp direction counts, then offsets
+    uint32_t dstart[28];
+    uint32_t item, ncand, total, out_base, chunk_first, npass, mask;
+};
+
+__device__ __forceinline__ int dir_dx(int d) { return d % 3 - 1; }
+__device__ __forceinline__ int dir_dy(int d) { return (d / 3) % 3 - 1; }
+__device__ __forceinline__ int dir_dz(int d) { return d / 9 - 1; }
+
+__device__ __forceinline__ void mark_clear(const FusedBufs &B, uint32_t g, uint32_t stamp, int slot) {
+    if (atomicExch(&B.gstamp[g], stamp) != stamp) B.clist[slot][atomicAdd(&B.ctrl->nclear[slot], 1u)] = g;
+}
+
+template <bool WRITE_VC>
+__global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, const ToolFrame *__restrict__ tools) {
+    __shared__ FusedSmem s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Ctrl *ctrl = B.ctrl;
+    const uint32_t step = *(volatile uint32_t *)&ctrl->step;
+    const int par = step & 1, m3 = step % 3;
+    const int m3n = (m3 + 1) % 3, m3c = (m3 + 2) % 3;
+    const PState in = par ? B.P[1] : B.P[0];
+    const PState out = par ? B.P[0] : B.P[1];
+    const Chunk *__restrict__ cin = par ? B.chunks[1] : B.chunks[0];
+    Chunk *__restrict__ cout = par ? B.chunks[0] : B.chunks[1];
+    const BlockTab *__restrict__ tin = par ? B.tabs[1] : B.tabs[0];
+    BlockTab *__restrict__ tout = par ? B.tabs[0] : B.tabs[1];
+    const float4 *__restrict__ Gcur = B.G[m3];
+    float4 *Gnext = B.G[m3n];
+    float4 *Gclr = B.G[m3c];
+    const uint32_t *__restrict__ act = B.alist[par];
+    uint32_t *act_next = B.alist[par ^ 1];
+    const uint32_t nact = *(volatile uint32_t *)&ctrl->nactive[par];
+    const uint32_t nclr = *(volatile uint32_t *)&ctrl->nclear[m3c];
+    const uint32_t *__restrict__ clr = B.clist[m3c];
+    const uint32_t nparticles = ctrl->n_particles;
+    const uint32_t nchunk_cap = B.nblocks + nparticles / T + 1;
+    const int nb = P.nb, n = P.n;
+    uint32_t err = 0;
+
+    if (tid < P.ntools * (int)(sizeof(ToolFrame) / 4))
+        reinterpret_cast<float *>(s.tools)[tid] = reinterpret_cast<const float *>(tools)[tid];
+
+    // 0. clear the grid blocks G_{k-1} touched, so that sub-step k+1 can scatter into it
+    for (uint32_t q = blockIdx.x * T + tid; q < nclr * 64u; q += gridDim.x * T)
+        Gclr[clr[q >> 6] * 64u + (q & 63u)] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s.item = atomicAdd(&ctrl->work, 1u);
+        __syncthreads();
+        const uint32_t item = s.item;
+        if (item >= nact) break;
+        const uint32_t b = act[item];
+        const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+
+        // 1. grid operation of the 6^3 G2P region
+        if (tid < 216) {
+            const int i = 4 * bx + tid % 6, j = 4 * by + (tid / 6) % 6, k = 4 * bz + tid / 36;
+            float3 v = make_float3(0.f, 0.f, 0.f);
+            if (i < n && j < n && k < n) {
+                const float4 g = Gcur[node_addr(i, j, k, nb)];
+                v = grid_node_update(g.x, g.y, g.z, g.w, i, j, k, P, s.tools);
+            }
+            s.v[tid] = make_float4(v.x, v.y, v.z, 0.f);
+        }
+        // runs heading to b: source lane l covers direction d = 26 - l, i.e.
+        // source block b - dir(d), in ascending source-block order
+        if (warp == 0) {
+            uint32_t np = 0, first = 0;
+            if (lane < 27) {
+                const int d = 26 - lane;
+                const int sx = bx - dir_dx(d), sy = by - dir_dy(d), sz = bz - dir_dz(d);
+                if (sx >= 0 && sy >= 0 && sz >= 0 && sx < nb && sy < nb && sz < nb) {
+                    const BlockTab t = tin[block_id(sx, sy, sz, nb)];
+                    if (t.stamp == step) { np = t.npass; first = t.first; }
+                }
+            }
+            uint32_t incl = np;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane < 27) { s.lane_first[lane] = first; s.lane_np[lane] = np; s.lane_off[lane] = incl - np; }
+            if (lane == 26) s.ncand = incl;
+        }
+        for (int q = tid; q < 2048; q += T) (&s.acc[0][0])[q] = 0.f;
+        for (int q = tid; q < 2 * NW * 28; q += T) (&s.wcnt[0][0][0])[q] = 0u;
+        __syncthreads();
+        uint32_t ncand = s.ncand;
+        if (ncand > CMAX) { ncand = CMAX; err |= kErrCapacity; }
+        for (uint32_t c = tid; c < ncand; c += T) {
+            int l = 0;
+            while (l < 26 && s.lane_off[l + 1] <= c) ++l;
+            const uint2 r = cin[s.lane_first[l] + (c - s.lane_off[l])].run[26 - l];
+            s.cand_start[c] = r.x;
+            s.cand_pre[c] = r.y;
+        }
+        __syncthreads();
+        // exclusive scan of run lengths (ncand <= 2 per thread)
+        {
+            const uint32_t c0 = 2 * tid, c1 = 2 * tid + 1;
+            const uint32_t l0 = c0 < ncand ? s.cand_pre[c0] : 0u, l1 = c1 < ncand ? s.cand_pre[c1] : 0u;
+            const uint32_t sum = l0 + l1;
+            uint32_t incl = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            __syncthreads();
+            if (lane == 31) s.wcnt[0][warp][0] = incl;
+            __syncthreads();
+            uint32_t wbase = 0, total = 0;
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t x = s.wcnt[0][w][0];
+                if (w < warp) wbase += x;
+                total += x;
+            }
+            const uint32_t e0 = wbase + incl - sum;
+            __syncthreads();
+            if (c0 < ncand) s.cand_pre[c0] = e0;
+            if (c1 < ncand) s.cand_pre[c1] = e0 + l0;
+            if (tid == 0) {
+                s.cand_pre[ncand] = total;
+                s.total = total;
+                const uint32_t npass = (total + T - 1) / T;
+                uint32_t ob = atomicAdd(&ctrl->part_alloc, total);
+                uint32_t cf = atomicAdd(&ctrl->chunk_alloc, npass);
+                if (ob + total > nparticles || cf + npass > nchunk_cap) {
+                    err |= kErrCapacity;
+                    s.npass = 0;
+                    BlockTab t; t.stamp = 0; t.first = 0; t.npass = 0; t.pad = 0;
+                    tout[b] = t;
+                } else {
+                    s.npass = npass;
+                    BlockTab t; t.stamp = step + 1; t.first = cf; t.npass = npass; t.pad = 0;
+                    tout[b] = t;
+                }
+                s.out_base = ob;
+                s.chunk_first = cf;
+                s.mask = 0;
+                s.wcnt[0][0][0] = 0u;
+                for (int w = 1; w < NW; ++w) s.wcnt[0][w][0] = 0u;
+            }
+        }
+        __syncthreads();
+        const uint32_t total = s.total, npass = s.npass, out_base = s.out_base, chunk_first = s.chunk_first;
+        const int ox = 4 * bx - 1, oy = 4 * by - 1, oz = 4 * bz - 1;   // arena origin
+
+        for (uint32_t pass = 0; pass < npass; ++pass) {
+            const uint32_t j = pass * T + tid;
+            const bool valid = j < total;
+            int d = 31;
+            float nxp = 0.f, nyp = 0.f, nzp = 0.f, idf = 0.f, Fn[9], Cm[9], vx = 0.f, vy = 0.f, vz = 0.f;
+            if (valid) {
+                // locate the run holding logical index j
+                int lo = 0, hi = (int)ncand - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s.cand_pre[mid] <= j) lo = mid; else hi = mid - 1;
+                }
+                const uint32_t src = s.cand_start[lo] + (j - s.cand_pre[lo]);
+                const float4 xi = in.xi[src];
+                const float4 a0 = in.f0[src], a1 = in.f1[src];
+                const float F[9] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, in.f2[src]};
+                idf = xi.w;
+                // --- G2P from the shared velocities
+                int gx, gy, gz;
+                const float fx = stencil_axis(xi.x, P.inv_dx, n, gx, err);
+                const float fy = stencil_axis(xi.y, P.inv_dx, n, gy, err);
+                const float fz = stencil_axis(xi.z, P.inv_dx, n, gz, err);
+                int lx = gx - 4 * bx, ly = gy - 4 * by, lz = gz - 4 * bz;
+                if (lx < 0 || lx > 3 || ly < 0 || ly > 3 || lz < 0 || lz > 3) {
+                    err |= kErrCfl;
+                    lx = min(max(lx, 0), 3); ly = min(max(ly, 0), 3); lz = min(max(lz, 0), 3);
+                }
+                float wx[3], wy[3], wz[3];
+                bspline_weights(fx, wx);
+                bspline_weights(fy, wy);
+                bspline_weights(fz, wz);
+                float B9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk) {
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) {
+                        const float wjk = wy[jj] * wz[kk];
+                        const float4 *row = &s.v[lx + 6 * (ly + jj) + 36 * (lz + kk)];
+                        float ax = 0.f, ay = 0.f, az = 0.f, bxx = 0.f, bxy = 0.f, bxz = 0.f;
+#pragma unroll
+                        for (int ii = 0; ii < 3; ++ii) {
+                            const float4 g = row[ii];
+                            const float wi = wx[ii], wo = wx[ii] * (ii - fx);
+                            ax += wi * g.x; ay += wi * g.y; az += wi * g.z;
+                            bxx += wo * g.x; bxy += wo * g.y; bxz += wo * g.z;
+                        }
+                        const float dy = wjk * (jj - fy), dz = wjk * (kk - fz);
+                        vx += wjk * ax; vy += wjk * ay; vz += wjk * az;
+                        B9[0] += wjk * bxx; B9[3] += wjk * bxy; B9[6] += wjk * bxz;
+                        B9[1] += dy * ax; B9[4] += dy * ay; B9[7] += dy * az;
+                        B9[2] += dz * ax; B9[5] += dz * ay; B9[8] += dz * az;
+                    }
+                }
+                const float cs = 4.0f * P.inv_dx;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) Cm[q] = cs * B9[q];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        Fn[3 * r + c] = F[3 * r + c] + P.dt * (Cm[3 * r] * F[c] + Cm[3 * r + 1] * F[3 + c] + Cm[3 * r + 2] * F[6 + c]);
+                nxp = xi.x + P.dt * vx;
+                nyp = xi.y + P.dt * vy;
+                nzp = xi.z + P.dt * vz;
+                if (!finite3(nxp, nyp, nzp)) {
+                    err |= kErrNumeric;
+                    nxp = xi.x; nyp = xi.y; nzp = xi.z;
+                }
+                // --- stress of the new state and P2G into the arena
+                float t[6];
+                kirchhoff(Fn, P.mu, P.lam, t, err);
+                const float m = P.mass, kst = P.stress_k, dxs = P.dx;
+                const float A[9] = {(m * Cm[0] - kst * t[0]) * dxs, (m * Cm[1] - kst * t[1]) * dxs, (m * Cm[2] - kst * t[2]) * dxs,
+                                    (m * Cm[3] - kst * t[1]) * dxs, (m * Cm[4] - kst * t[3]) * dxs, (m * Cm[5] - kst * t[4]) * dxs,
+                                    (m * Cm[6] - kst * t[2]) * dxs, (m * Cm[7] - kst * t[4]) * dxs, (m * Cm[8] - kst * t[5]) * dxs};
+                int hx, hy, hz;
+                const float ex = stencil_axis(nxp, P.inv_dx, n, hx, err);
+                const float ey = stencil_axis(nyp, P.inv_dx, n, hy, err);
+                const float ez = stencil_axis(nzp, P.inv_dx, n, hz, err);
+                bspline_weights(ex, wx);
+                bspline_weights(ey, wy);
+                bspline_weights(ez, wz);
+                const float qx = m * vx - (A[0] * ex + A[1] * ey + A[2] * ez);
+                const float qy = m * vy - (A[3] * ex + A[4] * ey + A[5] * ez);
+                const float qz = m * vz - (A[6] * ex + A[7] * ey + A[8] * ez);
+                const int ax0 = hx - ox, ay0 = hy - oy, az0 = hz - oz;
+                const bool in_arena = ax0 >= 0 && ax0 <= 5 && ay0 >= 0 && ay0 <= 5 && az0 >= 0 && az0 <= 5;
+                if (in_arena) {
+                    const int a0i = ax0 + 8 * ay0 + 64 * az0;
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk) {
+#pragma unroll
+                        for (int jj = 0; jj < 3; ++jj) {
+                            const float wjk = wy[jj] * wz[kk];
+                            const float rx = qx + A[1] * jj + A[2] * kk;
+                            const float ry = qy + A[4] * jj + A[5] * kk;
+                            const float rz = qz + A[7] * jj + A[8] * kk;
+#pragma unroll
+                            for (int ii = 0; ii < 3; ++ii) {
+                                const float w = wx[ii] * wjk;
+                                const int a = a0i + ii + 8 * jj + 64 * kk;
+                                atomicAdd(&s.acc[0][a], w * m);
+                                atomicAdd(&s.acc[1][a], w * (rx + A[0] * ii));
+                                atomicAdd(&s.acc[2][a], w * (ry + A[3] * ii));
+                                atomicAdd(&s.acc[3][a], w * (rz + A[6] * ii));
+                            }
+                        }
+                    }
+                } else {
+                    // moved further than one cell: scatter straight into G_{k+1}
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+                        for (int jj = 0; jj < 3; ++jj) {
+                            const float wjk = wy[jj] * wz[kk];
+                            const float rx = qx + A[1] * jj + A[2] * kk;
+                            const float ry = qy + A[4] * jj + A[5] * kk;
+                            const float rz = qz + A[7] * jj + A[8] * kk;
+#pragma unroll
+                            for (int ii = 0; ii < 3; ++ii) {
+                                const float w = wx[ii] * wjk;
+                                atomicAdd(&Gnext[node_addr(hx + ii, hy + jj, hz + kk, nb)],
+                                          make_float4(w * m, w * (rx + A[0] * ii), w * (ry + A[3] * ii), w * (rz + A[6] * ii)));
+                            }
+                        }
+                    for (int c = 0; c < 8; ++c) {
+                        const int gi = (hx + 2 * (c & 1)) >> 2, gj = (hy + (c & 2)) >> 2, gk = (hz + ((c >> 1) & 2)) >> 2;
+                        mark_clear(B, block_id(gi, gj, gk, nb), step + 1, m3n);
+                    }
+                }
+                // --- destination block of the new state
+                int ddx = (hx >> 2) - bx, ddy = (hy >> 2) - by, ddz = (hz >> 2) - bz;
+                if (ddx < -1 || ddx > 1 || ddy < -1 || ddy > 1 || ddz < -1 || ddz > 1) {
+                    err |= kErrCfl;
+                    ddx = min(max(ddx, -1), 1); ddy = min(max(ddy, -1), 1); ddz = min(max(ddz, -1), 1);
+                }
+                d = (ddx + 1) + 3 * (ddy + 1) + 9 * (ddz + 1);
+            }
+            // --- stable rank by direction within the pass
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+            uint32_t(*wc)[28] = s.wcnt[pass & 1];
+            if (valid && rank == 0) wc[warp][d] = __popc(peers);
+            __syncthreads();
+            for (int q = tid; q < NW * 28; q += T) (&s.wcnt[(pass + 1) & 1][0][0])[q] = 0u;
+            if (warp == 0) {
+                uint32_t run = 0;
+                if (lane < 27)
+                    for (int w = 0; w < NW; ++w) {
+                        const uint32_t c = wc[w][lane];
+                        wc[w][lane] = run;
+                        run += c;
+                    }
+                uint32_t incl = run;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const uint32_t pbase = out_base + pass * T;
+                if (lane < 27) {
+                    s.dstart[lane] = incl - run;
+                    cout[chunk_first + pass].run[lane] = make_uint2(pbase + incl - run, run);
+                }
+                const unsigned nz = __ballot_sync(0xffffffffu, lane < 27 && run > 0);
+                if (lane == 0) s.mask |= nz;
+            }
+            __syncthreads();
+            if (valid) {
+                const uint32_t pos = out_base + pass * T + s.dstart[d] + wc[warp][d] + rank;
+                out.xi[pos] = make_float4(nxp, nyp, nzp, idf);
+                out.f0[pos] = make_float4(Fn[0], Fn[1], Fn[2], Fn[3]);
+                out.f1[pos] = make_float4(Fn[4], Fn[5], Fn[6], Fn[7]);
+                out.f2[pos] = Fn[8];
+                if (WRITE_VC) store_vc(B.vc, pos, vx, vy, vz, Cm);
+            }
+        }
+        __syncthreads();
+        // 4. arena -> G_{k+1}
+        for (int q = tid; q < 512; q += T) {
+            const float am = s.acc[0][q], px = s.acc[1][q], py = s.acc[2][q], pz = s.acc[3][q];
+            if (am != 0.f || px != 0.f || py != 0.f || pz != 0.f) {
+                const int i = ox + (q & 7), jn = oy + ((q >> 3) & 7), k = oz + (q >> 6);
+                if (i >= 0 && jn >= 0 && k >= 0 && i < n && jn < n && k < n)
+                    atomicAdd(&Gnext[node_addr(i, jn, k, nb)], make_float4(am, px, py, pz));
+            }
+        }
+        // blocks of the next sub-step and grid blocks to clear before G_{k+1}'s reuse
+        if (warp == 0 && lane < 27) {
+            const int tx = bx + dir_dx(lane), ty = by + dir_dy(lane), tz = bz + dir_dz(lane);
+            if (tx >= 0 && ty >= 0 && tz >= 0 && tx < nb && ty < nb && tz < nb) {
+                const uint32_t tb = block_id(tx, ty, tz, nb);
+                if ((s.mask >> lane) & 1u) {
+                    if (atomicExch(&B.astamp[tb], step + 1) != step + 1)
+                        act_next[atomicAdd(&ctrl->nactive[par ^ 1], 1u)] = tb;
+                }
+                mark_clear(B, tb, step + 1, m3n);
+            }
+        }
+    }
+
+    if (err) atomicOr(&ctrl->err, err);
+    // last CTA: reset per-launch counters, advance the sub-step
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const uint32_t prev = atomicAdd(&ctrl->done, 1u);
+        if (prev == gridDim.x - 1) {
+            __threadfence();
+            if (*(volatile uint32_t *)&ctrl->part_alloc != nparticles) atomicOr(&ctrl->err, kErrCapacity);
+            ctrl->work = 0;
+            ctrl->part_alloc = 0;
+            ctrl->chunk_alloc = 0;
+            ctrl->nactive[par] = 0;
+            ctrl->nclear[m3c] = 0;
+            ctrl->done = 0;
+            __threadfence();
+            ctrl->step = step + 1;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, bool write_vc, int grid,
+                       cudaStream_t st) {
+    if (write_vc)
+        k_fused_step<true><<<grid, T, 0, st>>>(P, B, tools);
+    else
+        k_fused_step<false><<<grid, T, 0, st>>>(P, B, tools);
+}
+
+int fused_step_occupancy(int threads) {
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fused_step<true>, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_step<false>, threads, 0);
+    return a < b ? a : b;
+}
+
+}  // namespace gbmpm

@@ -1,0 +1,66 @@
+// launch.h -- host-side launchers of the library's kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gbmpm {
+
+// kernels_split.cu
+void launch_p2g_scatter(const DevParams &P, const PState &S, const VCState &V, uint32_t n, float4 *G, Ctrl *ctrl,
+                        int grid, cudaStream_t st);
+void launch_grid_update_dense(const DevParams &P, float4 *G, const ToolFrame *tools, int grid, cudaStream_t st);
+void launch_g2p_split(const DevParams &P, const PState &S, const VCState &V, uint32_t n, const float4 *G, Ctrl *ctrl,
+                      int grid, cudaStream_t st);
+void launch_load_identity(const float *x, const float *v, const float *F, const float *C, uint32_t n, const PState &S,
+                          const VCState &V, Ctrl *ctrl, int grid, cudaStream_t st);
+void launch_read_out(const PState &S, const VCState &V, uint32_t n, float *x, float *v, float *F, float *C, int grid,
+                     cudaStream_t st);
+void launch_grid_to_dense(int n, int nb, const float4 *G, float4 *out, int grid, cudaStream_t st);
+void launch_grid_velocity_dense(const DevParams &P, const float4 *G, const ToolFrame *tools, float *out, int grid,
+                                cudaStream_t st);
+
+// kernels_sort.cu: stable counting sort of particles by grid block at load.
+struct SortScratch {
+    uint32_t *keys;     // n
+    uint32_t *counts;   // nblocks
+    uint32_t *offsets;  // nblocks + 1
+    uint32_t *cursor;   // nblocks
+    uint32_t *perm;     // n: slot -> particle index
+};
+// keys/counts/offsets/perm of the stable counting sort of particles by the
+// block of floor(x/dx - 0.5) (x: n x 3 row-major, device).  counts must be
+// zero on entry.
+void launch_block_sort(const DevParams &P, const float *x, uint32_t n, const SortScratch &s, Ctrl *ctrl, int grid,
+                       cudaStream_t st);
+// Place particle perm[j] in slot j and build the run tables of sub-step
+// `step` (one chunk per non-empty block, index = block id).
+struct FusedBufs;
+void launch_place_sorted(const DevParams &P, const float *x, const float *v, const float *F, const float *C,
+                         uint32_t n, const SortScratch &s, const PState &S, const VCState &V, int grid,
+                         cudaStream_t st);
+void launch_init_tables(const DevParams &P, const SortScratch &s, const FusedBufs &B, uint32_t step, int grid,
+                        cudaStream_t st);
+
+// kernel_fused.cu
+struct FusedBufs {
+    PState P[2];
+    VCState vc;               // v and C of the last sub-step of a call, slot-aligned with P[current]
+    Chunk *chunks[2];
+    BlockTab *tabs[2];
+    uint32_t *alist[2];       // active blocks by sub-step parity
+    uint32_t *clist[3];       // grid blocks to clear, by sub-step mod 3
+    float4 *G[3];             // grid buffers by sub-step mod 3
+    uint32_t *astamp;         // per block: last sub-step it was put on an active list
+    uint32_t *gstamp;         // per block: last sub-step it was put on a clear list
+    Ctrl *ctrl;
+    uint32_t nblocks;
+};
+void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, bool write_vc, int grid,
+                       cudaStream_t st);
+int fused_step_occupancy(int threads);
+constexpr int kFusedThreads = 256;
+
+}  // namespace gbmpm

@@ -1,0 +1,352 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, on
+the same seeded FP32 inputs, element by element.
+
+Tolerances (FP32 arithmetic against FP64, derived in the design notes):
+grid mass and momentum after P2G 1e-5 of the largest magnitude; grid
+velocities 1e-5; one sub-step of particle state: x 1e-6 absolute, v 1e-5 and
+C 2e-4 relative, F 1e-5; 200-step trajectories: x 1e-3 dx, F 1e-4.  Integer
+work (block keys, the sort order) is compared bit for bit.  Where the grid
+operation branches (contact threshold, approaching test, friction clamp,
+closest tool) within 1e-5 of the branch point, FP32 and FP64 may branch
+differently; those nodes, and the particles whose stencil touches them, are
+left out and counted.
+"""
+import numpy as np
+import pytest
+
+import helpers as H
+from oracle import oracle as O
+from paper_2402_01181_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2402_01181_gb300 import mpm
+    return mpm
+
+
+def _tool_scene(seed=0):
+    """cube8k particles with random (v, C, F), a rotated capsule and a box
+    cutting into the cube, both moving."""
+    sc = H.perturbed_scene(scenes.cube8k(seed), seed=seed + 1)
+    cap = scenes.capsule_shape(0.06, 0.08)
+    box = scenes.box_shape(0.08, 0.05, 0.07)
+    p_cap0 = np.array([0.47, 0.57, 0.51, 0.3, 0.1, 0.2])
+    p_box0 = np.array([0.55, 0.40, 0.45, 0.0, 0.4, 0.1])
+    vel_cap = np.array([0.2, -1.5, 0.1, 20.0, -10.0, 5.0])     # per second; rotation in rad/s
+    vel_box = np.array([-0.5, 1.0, 0.3, 0.0, 30.0, -15.0])
+    dt = sc.dt
+    sc.tools = [scenes.Tool(cap, lambda s: p_cap0 + vel_cap * dt * (s + 1)),
+                scenes.Tool(box, lambda s: p_box0 + vel_box * dt * (s + 1))]
+    sc.friction = 0.4
+    return sc
+
+
+# ------------------------------------------------------------------- P2G
+
+@pytest.mark.parametrize("pipe", H.PIPELINES)
+def test_p2g_grid_parity(M, pipe):
+    sc = H.perturbed_scene(scenes.cube8k(), seed=11)
+    sim = M.sim_from_scene(sc, pipeline=H.pipeline_id(pipe))
+    g = sim.read_grid().astype(np.float64)
+    out = sim.read()
+    sim.close()
+    st = H.oracle_state(out)
+    gm, gmv = O.p2g(O.OracleParams.from_scene(sc), st)
+    assert H.rel_err(g[..., 0], gm) <= 1e-5
+    assert H.rel_err(g[..., 1:], gmv) <= 1e-5
+    assert abs(g[..., 0].sum() - sc.n * sc.rho * sc.particle_volume) <= 1e-5 * sc.n * sc.rho * sc.particle_volume
+
+
+# ------------------------------------------------------- grid operation
+
+@pytest.mark.parametrize("pipe", H.PIPELINES)
+def test_grid_operation_parity(M, pipe):
+    sc = _tool_scene()
+    sim = M.sim_from_scene(sc, pipeline=H.pipeline_id(pipe))
+    for t, tool in enumerate(sc.tools):
+        sim.set_tool(t, tool.pose(0), tool.shape)
+    g = sim.read_grid().astype(np.float64)
+    gv = sim.grid_velocity().astype(np.float64)
+    sim.close()
+    prm = O.OracleParams.from_scene(sc)
+    frames, nt = O.frames_for_steps(sc.tools, 0, 1, sc.dt, 1)
+    ov, contact, margin = O.grid_update(prm, g[..., 0].copy(), g[..., 1:].copy(), frames, nt)
+    mask = margin < 1e-5
+    ncontact = int((contact >= 0).sum())
+    assert ncontact > 50, "the tools must touch the material"
+    assert mask.sum() <= max(5, 0.03 * ncontact)
+    vmax = np.abs(ov).max()
+    diff = np.abs(gv - ov).max(axis=-1)
+    assert diff[~mask].max() <= 1e-5 * vmax
+
+
+# ----------------------------------------------------------- one sub-step
+
+@pytest.mark.parametrize("pipe", H.PIPELINES)
+def test_single_substep_parity_with_tools(M, pipe):
+    sc = _tool_scene(seed=2)
+    sim = M.sim_from_scene(sc, pipeline=H.pipeline_id(pipe))
+    start = sim.read()
+    for t, tool in enumerate(sc.tools):
+        sim.set_tool(t, tool.pose(0), tool.shape)
+    sim.step(1)
+    out = sim.read()
+    sim.close()
+    st = H.oracle_state(start)
+    mask = H.contact_mask_nodes(sc, st, 0)
+    skip = H.particles_touching(mask, st.x, sc.n_grid)
+    H.oracle_steps(sc, st, 0, 1, call_len=1)
+    assert mask.sum() <= 5
+    ok, errs = H.compare_particles(out, st, sc.dx, skip)
+    assert ok, errs
+
+
+@pytest.mark.parametrize("pipe", H.PIPELINES)
+def test_fused_and_split_agree_on_many_substeps(M, pipe):
+    """25 sub-steps in one call (one frame of the paper's loop) with moving
+    tools, the tool frames interpolated inside the call."""
+    sc = _tool_scene(seed=3)
+    sim = M.sim_from_scene(sc, pipeline=H.pipeline_id(pipe))
+    for t, tool in enumerate(sc.tools):
+        sim.set_tool(t, tool.pose(24), tool.shape)
+    sim.step(25)
+    out = sim.read()
+    sim.close()
+    st = O.State(sc.x, sc.v, sc.C, sc.F)
+    H.oracle_steps(sc, st, 0, 25, call_len=25)
+    # contact branches may flip over 25 sub-steps; require agreement on the
+    # bulk and bound the rest
+    dxp = np.abs(out["x"] - st.x).max(axis=1)
+    assert np.quantile(dxp, 0.99) <= 1e-4 * sc.dx
+    assert dxp.max() <= 1e-2 * sc.dx
+
+
+# ------------------------------------------------------- trajectories
+
+@pytest.mark.parametrize("pipe", H.PIPELINES)
+def test_cube8k_200_substeps(M, pipe):
+    """The 8,192-particle cube over 200 sub-steps (free fall): against the
+    oracle and against the symplectic-Euler closed form."""
+    sc = scenes.cube8k()
+    sim = M.sim_from_scene(sc, pipeline=H.pipeline_id(pipe))
+    sim.step(200)
+    out = sim.read()
+    sim.close()
+    st = O.State(sc.x)
+    H.oracle_steps(sc, st, 0, 200)
+    assert np.abs(out["x"] - st.x).max() <= 1e-3 * sc.dx
+    assert np.abs(out["F"] - st.F).max() <= 1e-4
+    g = np.array(sc.gravity)
+    k = 200
+    assert np.abs(out["x"] - (sc.x.astype(np.float64) + g * sc.dt ** 2 * k * (k + 1) / 2)).max() <= 1e-3 * sc.dx
+    assert np.abs(out["v"] - k * g * sc.dt).max() <= 1e-4 * k * 9.8 * sc.dt
+
+
+def test_slab30k_sampled_single_steps(M):
+    """The 30K-particle slab pressed and dragged by the capsule over 2,000
+    sub-steps; at sampled sub-steps one sub-step is compared from the shared
+    state (contact-rich: trajectories are not pinned beyond one sub-step)."""
+    sc = scenes.slab30k()
+    sim = M.sim_from_scene(sc)
+    tool = sc.tools[0]
+    s = 0
+    checked = 0
+    for sample in (0, 400, 1000, 1400, 1975):
+        while s < sample:
+            m = min(25, sample - s)
+            sim.set_tool(0, tool.pose(s + m - 1), tool.shape)
+            sim.step(m)
+            s += m
+        state = sim.read()
+        sim.set_tool(0, tool.pose(s), tool.shape)
+        sim.step(1)
+        out = sim.read()
+        st = H.oracle_state(state)
+        mask = H.contact_mask_nodes(sc, st, s)
+        skip = H.particles_touching(mask, st.x, sc.n_grid)
+        frames, nt = O.frames_for_steps(sc.tools, s, 1, sc.dt, 1)
+        O.run(O.OracleParams.from_scene(sc), st, 1, frames, nt)
+        ok, errs = H.compare_particles(out, st, sc.dx, skip)
+        assert ok, (sample, errs)
+        assert mask.sum() <= 5
+        s += 1
+        checked += 1
+    sim.close()
+    assert checked == 5
+
+
+def test_block1m_single_step_full_size(M):
+    """The 1M-particle roofline workload, in the configuration the benchmark
+    times (one 25-sub-step call, then one more sub-step compared in full)."""
+    sc = scenes.block1m()
+    sim = M.sim_from_scene(sc)
+    tool = sc.tools[0]
+    sim.set_tool(0, tool.pose(24), tool.shape)
+    sim.step(25)
+    state = sim.read()
+    sim.set_tool(0, tool.pose(25), tool.shape)
+    sim.step(1)
+    out = sim.read()
+    sim.close()
+    st = H.oracle_state(state)
+    mask = H.contact_mask_nodes(sc, st, 25)
+    skip = H.particles_touching(mask, st.x, sc.n_grid)
+    frames, nt = O.frames_for_steps(sc.tools, 25, 1, sc.dt, 1)
+    O.run(O.OracleParams.from_scene(sc), st, 1, frames, nt)
+    ok, errs = H.compare_particles(out, st, sc.dx, skip)
+    assert ok, errs
+    assert mask.sum() <= 10
+
+
+# --------------------------------------------------------------- sorting
+
+def test_sort_order_is_the_stable_counting_sort(M):
+    """After a load the order is the stable sort of particle indices by block
+    key; after every sub-step it is the stable re-sort of the previous order
+    by the new keys.  Compared bit for bit."""
+    sc = scenes.cube8k(seed=5)
+    sc.E = 0.0
+    sc.v = np.tile(np.array([[60.0, -40.0, 50.0]], np.float32), (sc.n, 1))   # 0.1-0.2 dx per sub-step
+    sim = M.sim_from_scene(sc)
+    ids, keys = sim.read_order()
+    x = sim.read()["x"]
+    k_ref = O.block_keys(sc.n_grid, x)
+    assert np.array_equal(ids, O.sorted_order(k_ref))
+    assert np.array_equal(keys, k_ref[ids])
+    moved = 0
+    for _ in range(10):
+        prev = ids.copy()
+        prev_keys = k_ref.copy()
+        sim.step(1)
+        ids, keys = sim.read_order()
+        x = sim.read()["x"]
+        k_ref = O.block_keys(sc.n_grid, x)
+        assert np.array_equal(ids, O.sorted_order(k_ref, prev))
+        assert np.array_equal(keys, k_ref[ids])
+        moved += int((k_ref != prev_keys).sum())
+    sim.close()
+    assert moved > 500, "the test must move particles across blocks"
+
+
+# ------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("pipe", H.PIPELINES)
+@pytest.mark.parametrize("count", [0, 1, 37, 257, 1000])
+def test_ragged_and_tiny_counts(M, pipe, count):
+    sc = H.perturbed_scene(scenes.cube8k(), seed=7)
+    rng = np.random.default_rng(count)
+    idx = np.sort(rng.choice(sc.n, size=count, replace=False))
+    x, v, C, F = sc.x[idx], sc.v[idx], sc.C[idx], sc.F[idx]
+    sub = scenes.Scene("sub", n_grid=sc.n_grid, dt=sc.dt, E=sc.E, nu=sc.nu, rho=sc.rho, x=x,
+                       particle_volume=sc.particle_volume, v=v, C=C, F=F)
+    sim = M.sim_from_scene(sub, pipeline=H.pipeline_id(pipe), max_particles=max(count, 1))
+    sim.step(3)
+    out = sim.read()
+    sim.close()
+    st = O.State(x, v, C, F)
+    H.oracle_steps(sub, st, 0, 3)
+    if count:
+        ok, errs = H.compare_particles(out, st, sub.dx, tol_x=3e-6, tol_v=3e-5, tol_C=5e-4, tol_F=3e-5)
+        assert ok, errs
+
+
+def test_crowded_block_uses_many_passes(M):
+    """20,000 particles inside one 4^3-cell block (~310 per cell): the load
+    sort takes its large-segment path and the fused sub-step needs 79 passes
+    and a multi-chunk run table on the next sub-step."""
+    n = 32
+    rng = np.random.default_rng(9)
+    x = (np.array([16.5, 16.5, 16.5]) + 3.99 * rng.random((20000, 3))) / n   # all stencil bases in block (4,4,4)
+    x = x.astype(np.float32)
+    v, C, F = scenes.random_state(x, 10, v_scale=0.2, c_scale=0.5, f_dev=0.02)
+    sc = scenes.Scene("crowd", n_grid=n, dt=1e-5, E=1e3, nu=0.3, rho=1e3, x=x,
+                      particle_volume=(1.0 / n) ** 3 / 300, v=v, C=C, F=F)
+    sim = M.sim_from_scene(sc)
+    ids, keys = sim.read_order()
+    assert np.array_equal(ids, np.arange(20000))
+    sim.step(3)
+    out = sim.read()
+    ids, keys = sim.read_order()
+    sim.close()
+    st = O.State(x, v, C, F)
+    H.oracle_steps(sc, st, 0, 3)
+    ok, errs = H.compare_particles(out, st, sc.dx, tol_v=3e-5, tol_C=5e-4)
+    assert ok, errs
+    assert np.array_equal(np.sort(ids), np.arange(20000))
+
+
+def test_error_flags(M):
+    sc = scenes.cube8k()
+    # a particle whose stencil leaves the grid
+    x = sc.x.copy()
+    x[5] = (0.001, 0.5, 0.5)
+    bad = scenes.Scene("edge", n_grid=32, dt=1e-4, E=5e3, nu=0.3, rho=1e3, x=x, particle_volume=sc.particle_volume)
+    for pipe in H.PIPELINES:
+        sim = M.sim_from_scene(bad, pipeline=H.pipeline_id(pipe))
+        if pipe == "fused":                       # the load's block sort sees it first
+            assert sim.status() == M.MPM_ERR_DOMAIN
+            with pytest.raises(M.MPMError) as ei:  # reported again by the next call
+                sim.step(1)
+            assert ei.value.status == M.MPM_ERR_DOMAIN
+            sim.clear_error()
+            assert sim.status() == M.MPM_OK
+        sim.step(1)
+        assert sim.status() == M.MPM_ERR_DOMAIN
+        sim.close()
+    # non-finite input
+    x = sc.x.copy()
+    x[7, 1] = np.nan
+    for pipe in H.PIPELINES:
+        sim = M.sim_from_scene(scenes.Scene("nan", n_grid=32, dt=1e-4, E=5e3, nu=0.3, rho=1e3, x=x,
+                                            particle_volume=sc.particle_volume), pipeline=H.pipeline_id(pipe))
+        _step_expecting(M, sim, M.MPM_ERR_NUMERIC)
+        assert sim.status() == M.MPM_ERR_NUMERIC
+        sim.close()
+    # inverted particle: det F < 0 is clamped inside ln and flagged
+    F = np.tile(np.eye(3).reshape(1, 9), (sc.n, 1)).astype(np.float32)
+    F[3] = np.diag([1.0, 1.0, -1.0]).reshape(9)
+    for pipe in H.PIPELINES:
+        sim = M.sim_from_scene(scenes.Scene("inv", n_grid=32, dt=1e-4, E=5e3, nu=0.3, rho=1e3, x=sc.x, F=F,
+                                            particle_volume=sc.particle_volume), pipeline=H.pipeline_id(pipe))
+        _step_expecting(M, sim, M.MPM_ERR_NUMERIC)
+        with pytest.raises(M.MPMError) as ei:
+            sim.read()
+        assert ei.value.status == M.MPM_ERR_NUMERIC
+        sim.close()
+
+
+def _step_expecting(M, sim, status):
+    """Step once; a sticky error raised earlier may already be reported here."""
+    try:
+        sim.step(1)
+    except M.MPMError as e:
+        assert e.status == status
+
+
+def test_api_contract(M):
+    sc = scenes.cube8k()
+    sim = M.sim_from_scene(sc)
+    h = sim.h
+    import ctypes as ct
+    assert M.mpm_step(h, -1) == M.MPM_ERR_ARG
+    assert M.mpm_load_particles(h, sc.n + 1, None, None, None, None, ct.c_float(1.0), 0) == M.MPM_ERR_ARG
+    bad_shape = np.array([7, 0.1, 0.1, 0.1, 0, 0, 0, 0], np.float32)
+    pose = np.zeros(6, np.float64)
+    assert M.mpm_set_tool_pose(h, 0, pose.ctypes.data_as(M._DP), bad_shape.ctypes.data_as(M._FP)) == M.MPM_ERR_ARG
+    assert M.mpm_set_tool_pose(h, 9, pose.ctypes.data_as(M._DP), bad_shape.ctypes.data_as(M._FP)) == M.MPM_ERR_ARG
+    n = ct.c_int64()
+    assert M.mpm_num_particles(h, ct.byref(n)) == 0 and n.value == sc.n
+    sim.step(4)
+    assert M.mpm_substeps_taken(h, ct.byref(n)) == 0 and n.value == 4
+    # load/read round trip is exact (checkpoint / resume)
+    out = sim.read()
+    sim.load(out["x"], sc.particle_volume, out["v"], out["F"], out["C"])
+    again = sim.read()
+    for k in out:
+        assert np.array_equal(out[k], again[k])
+    sim.close()
