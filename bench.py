@@ -61,13 +61,6 @@ def parse():
 
 # --------------------------------------------------------------- helpers
 
-def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
-
-
 def kernel_source_sha():
     h = hashlib.sha256()
     for f in ("kernel_fused.cu", "common.cuh"):
@@ -147,7 +140,8 @@ def run_gpu_workload(name, args, rank, device, barrier, max_over_ranks, with_e2e
     from paper_2402_01181_gb300 import mpm
     steps = steps or args.steps
     S = args.substeps
-    sc = scenes.SCENES[name](seed=rank)
+    from paper_2402_01181_gb300 import dist as D
+    sc = scenes.SCENES[name](seed=D.replica_seed(rank))
     pipe = mpm.MPM_PIPELINE_FUSED if args.pipeline == "fused" else mpm.MPM_PIPELINE_SPLIT
     stream = torch.cuda.current_stream(device)
     sim = mpm.sim_from_scene(sc, pipeline=pipe)
@@ -235,7 +229,8 @@ def time_oracle(name, budget_s, rank_seed=0, max_steps=50):
 
 
 def reference_main(args):
-    world, rank, local = dist_env()
+    from paper_2402_01181_gb300 import dist as D
+    world, rank, local = D.env()
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
@@ -275,26 +270,12 @@ def main():
     if args.impl == "reference":
         return reference_main(args)
     import torch
-    world, rank, local = dist_env()
+    from paper_2402_01181_gb300 import dist as D
+    world, rank, local = D.env()
     device = local if torch.cuda.device_count() > local else 0
     torch.cuda.set_device(device)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", device))
-
-        def barrier():
-            dist.barrier()
-
-        def max_over_ranks(v):
-            t = torch.tensor([float(v)], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-    else:
-        def barrier():
-            pass
-
-        def max_over_ranks(v):
-            return float(v)
+    ranks = D.Ranks(device=device)
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     import __graft_entry__ as ge
     ge.build()
@@ -313,9 +294,7 @@ def main():
                   "e2e": r2["n"] * S * r2["steps"] * world / (r2["t_e2e_ms"] / 1e3)}
 
     if rank != 0:
-        if world > 1:
-            import torch.distributed as dist
-            dist.destroy_process_group()
+        ranks.close()
         return
 
     peak, peak_kind = measured_peak()
@@ -356,9 +335,7 @@ def main():
         "secondary": second,
     }
     print(json.dumps(line))
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    ranks.close()
 
 
 if __name__ == "__main__":

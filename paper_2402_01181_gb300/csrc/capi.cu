@@ -409,6 +409,7 @@ mpm_status mpm_create(const mpm_config *cfg, void *cuda_stream, mpm_alloc_fn all
             if ((st = dalloc_t(h, &h->fb.chunks[b], h->chunk_cap)) != MPM_OK) return bail(st);
             if ((st = dalloc_t(h, &h->fb.tabs[b], h->nblocks)) != MPM_OK) return bail(st);
             if ((st = dalloc_t(h, &h->fb.alist[b], h->nblocks)) != MPM_OK) return bail(st);
+            if ((st = dalloc_t(h, &h->fb.inbox[b], (size_t)h->nblocks * kInbox)) != MPM_OK) return bail(st);
         }
         for (int b = 0; b < 3; ++b)
             if ((st = dalloc_t(h, &h->fb.clist[b], h->nblocks)) != MPM_OK) return bail(st);
@@ -432,8 +433,10 @@ mpm_status mpm_create(const mpm_config *cfg, void *cuda_stream, mpm_alloc_fn all
     e = cudaEventRecord(h->ev_frames, h->stream);
     if (e == cudaSuccess && h->fb.astamp) e = cudaMemsetAsync(h->fb.astamp, 0, sizeof(uint32_t) * h->nblocks, h->stream);
     if (e == cudaSuccess && h->fb.gstamp) e = cudaMemsetAsync(h->fb.gstamp, 0, sizeof(uint32_t) * h->nblocks, h->stream);
-    for (int b = 0; b < 2 && e == cudaSuccess && h->fb.tabs[b]; ++b)
+    for (int b = 0; b < 2 && e == cudaSuccess && h->fb.tabs[b]; ++b) {
         e = cudaMemsetAsync(h->fb.tabs[b], 0, sizeof(BlockTab) * h->nblocks, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->fb.inbox[b], 0, sizeof(uint4) * h->nblocks * kInbox, h->stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->fb.ctrl, 0, sizeof(Ctrl), h->stream);
     if (e != cudaSuccess) return bail(fail(MPM_ERR_CUDA, "initial clears: %s", cudaGetErrorString(e)));
     *out = h;

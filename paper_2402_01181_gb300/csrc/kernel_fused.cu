@@ -9,17 +9,25 @@
 //   1. grid operation (Eq. 7, gravity, tool contact Eqs. 11, 15-19, walls) of
 //      the 6^3 nodes that the stencils of b's particles touch, into shared
 //      memory;
-//   2. per particle: G2P (Eqs. 8-9), F update (Eq. 4), advection (Eq. 10),
-//      Kirchhoff stress of the new F (Eqs. 5-6) and the affine momentum
-//      A = m C - dt V^0 (4/dx^2) tau, then P2G (Eqs. 1-3) of the new state
-//      into an 8^3-node shared-memory arena around b (global atomics for a
-//      particle that moved further than one cell);
-//   3. a stable counting sort of the particles by their new block: every
-//      256-particle pass writes its particles grouped by the direction
-//      (-1..1)^3 to their new block, and records where each group starts;
-//      the next sub-step's CTA for block b' reads the runs heading to b' from
-//      its 27 neighbours, in ascending source-block order;
-//   4. the arena is added to G_{k+1} with float4 atomics.
+//   2. per particle (256-particle passes): G2P (Eqs. 8-9), F update (Eq. 4),
+//      advection (Eq. 10), Kirchhoff stress of the new F (Eqs. 5-6) and the
+//      affine momentum A = m C - dt V^0 (4/dx^2) tau;
+//   3. a stable counting sort of the particles by their new block: every pass
+//      writes its particles grouped by the direction (-1..1)^3 to their new
+//      block and records where each group starts; the next sub-step's CTA for
+//      block b' reads the runs heading to b' from its 27 neighbours, in
+//      ascending source-block order;
+//   4. P2G (Eqs. 1-3) of up to 512 new particle states at a time into an
+//      8^3-node shared arena around b.  The arena accumulates in 32-bit fixed
+//      point with native shared integer atomics (shared float atomics are
+//      several times slower): mass in units of m_p 2^-22, momentum in units of
+//      B 2^-22 where B bounds every contribution of the group, so no
+//      contribution exceeds 2^22 and no node sum of <= 512 particles can
+//      overflow; the integer sums are exact, hence independent of the order of
+//      the atomics.  A particle that moved further than one cell scatters
+//      straight into G_{k+1} with float atomics instead.
+//   5. the arena is converted back to floats and added to G_{k+1} with float4
+//      atomics.
 //
 // Grid buffers rotate over three slots (read G_k, write G_{k+1}, clear
 // G_{k-1} for reuse), particle buffers and run tables over two; the last CTA
@@ -33,18 +41,34 @@ namespace {
 
 constexpr int T = kFusedThreads;
 constexpr int NW = T / 32;
-constexpr int CMAX = 512;   // run candidates (source chunk x direction) per block
+constexpr int CMAX = 512;      // run candidates (source chunk x direction) per block
+constexpr int GROUP = 2 * T;   // particles staged per arena flush
+constexpr float kFix = 4194304.0f;      // 2^22
+constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23: float -> nearest int for |v| < 2^22
+// arena node (x, y, z) in [0,8)^3 sits at x + kAy y + kAz z: kAz = 68 keeps the
+// bases of a z-pair of cells in distinct shared-memory banks
+constexpr int kAy = 8, kAz = 68, kArena = 8 * kAz;
 
 struct FusedSmem {
-    float4 v[216];               // grid velocities of nodes [4b, 4b+5]^3
-    float acc[4][512];           // P2G arena over nodes [4b-1, 4b+6]^3: m, mv_x, mv_y, mv_z
+    // double-buffered per-block inputs, prefetched with cp.async one block ahead:
+    // the 6^3 grid nodes [4b, 4b+5]^3 (mass, momentum; turned into velocities
+    // in place by the grid operation) and the block's inbox of incoming runs
+    float4 graw[2][216];
+    uint4 inbox[2][kInbox];
+    uint32_t items[2], bids[2];
+    int acc[4][kArena];            // P2G arena over nodes [4b-1, 4b+6]^3 (fixed point, padded strides)
+    // staged P2G inputs of one group: packed arena base, fx (3), q (3), A dx (9)
+    int st_base[GROUP];
+    float st_f[3][GROUP];
+    float st_q[3][GROUP];
+    float st_a[9][GROUP];
     ToolFrame tools[kMaxTools];
-    uint32_t cand_start[CMAX];   // first slot of each run
-    uint32_t cand_pre[CMAX + 1]; // exclusive prefix of run lengths
-    uint32_t lane_first[27], lane_np[27], lane_off[27];
-    uint32_t wcnt[2][NW][28];    // per pass parity: per-warp direction counts, then offsets
+    uint32_t cand_start[CMAX];     // first slot of each run
+    uint32_t cand_pre[CMAX + 1];   // exclusive prefix of run lengths
+    uint32_t lane_first[27], lane_off[27];
+    uint32_t wcnt[2][NW][28];      // per pass parity: per-warp direction counts, then offsets
     uint32_t dstart[28];
-    uint32_t item, ncand, total, out_base, chunk_first, npass, mask;
+    uint32_t ncand, total, out_base, chunk_first, npass, mask, bmax;
 };
 
 __device__ __forceinline__ int dir_dx(int d) { return d % 3 - 1; }
@@ -55,9 +79,41 @@ __device__ __forceinline__ void mark_clear(const FusedBufs &B, uint32_t g, uint3
     if (atomicExch(&B.gstamp[g], stamp) != stamp) B.clist[slot][atomicAdd(&B.ctrl->nclear[slot], 1u)] = g;
 }
 
+// nearest integer of v (|v| < 2^22) via the float mantissa
+__device__ __forceinline__ int fix_round(float scaled_plus_magic) {
+    return __float_as_int(scaled_plus_magic) - 0x4B400000;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    const int bytes = valid ? 16 : 0;   // 0: fill with zeros, read nothing
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Start copying block b's grid region of G_k and its inbox into buffer buf.
+__device__ __forceinline__ void prefetch_block(FusedSmem &s, int buf, uint32_t b, const uint4 *__restrict__ inbox_in,
+                                               const float4 *__restrict__ Gcur, int nb, int n, int tid) {
+    const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+    for (int q = tid; q < 216 + kInbox; q += T) {
+        if (q < 216) {
+            const int i = 4 * bx + q % 6, j = 4 * by + (q / 6) % 6, k = 4 * bz + q / 36;
+            const bool ok = i < n && j < n && k < n;
+            cp_async16(&s.graw[buf][q], ok ? (const void *)&Gcur[node_addr(i, j, k, nb)] : (const void *)Gcur, ok);
+        } else {
+            const int e = q - 216;
+            cp_async16(&s.inbox[buf][e], &inbox_in[(size_t)b * kInbox + e], true);
+        }
+    }
+    cp_async_commit();
+}
+
+
 template <bool WRITE_VC>
-__global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, const ToolFrame *__restrict__ tools) {
-    __shared__ FusedSmem s;
+__global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, const ToolFrame *__restrict__ tools) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FusedSmem &s = *reinterpret_cast<FusedSmem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Ctrl *ctrl = B.ctrl;
     const uint32_t step = *(volatile uint32_t *)&ctrl->step;
@@ -72,6 +128,8 @@ __global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, c
     const float4 *__restrict__ Gcur = B.G[m3];
     float4 *Gnext = B.G[m3n];
     float4 *Gclr = B.G[m3c];
+    const uint4 *__restrict__ inbox_in = par ? B.inbox[1] : B.inbox[0];
+    uint4 *__restrict__ inbox_out = par ? B.inbox[0] : B.inbox[1];
     const uint32_t *__restrict__ act = B.alist[par];
     uint32_t *act_next = B.alist[par ^ 1];
     const uint32_t nact = *(volatile uint32_t *)&ctrl->nactive[par];
@@ -80,6 +138,7 @@ __global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, c
     const uint32_t nparticles = ctrl->n_particles;
     const uint32_t nchunk_cap = B.nblocks + nparticles / T + 1;
     const int nb = P.nb, n = P.n;
+    const float m = P.mass;
     uint32_t err = 0;
 
     if (tid < P.ntools * (int)(sizeof(ToolFrame) / 4))
@@ -89,111 +148,143 @@ __global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, c
     for (uint32_t q = blockIdx.x * T + tid; q < nclr * 64u; q += gridDim.x * T)
         Gclr[clr[q >> 6] * 64u + (q & 63u)] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) s.item = atomicAdd(&ctrl->work, 1u);
-        __syncthreads();
-        const uint32_t item = s.item;
-        if (item >= nact) break;
-        const uint32_t b = act[item];
-        const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+    // prologue: first work item and its inputs
+    if (tid == T - 1) {
+        const uint32_t it = atomicAdd(&ctrl->work, 1u);
+        s.items[0] = it;
+        s.bids[0] = it < nact ? act[it] : 0u;
+    }
+    __syncthreads();
+    if (s.items[0] < nact) prefetch_block(s, 0, s.bids[0], inbox_in, Gcur, nb, n, tid);
+    cp_async_wait_all();
+    __syncthreads();
 
-        // 1. grid operation of the 6^3 G2P region
-        if (tid < 216) {
-            const int i = 4 * bx + tid % 6, j = 4 * by + (tid / 6) % 6, k = 4 * bz + tid / 36;
+    for (int cb = 0;; cb ^= 1) {
+        const uint32_t item = s.items[cb];
+        if (item >= nact) break;
+        const uint32_t b = s.bids[cb];
+        const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+        // the next work item, fetched while this block is set up
+        if (tid == T - 1) {
+            const uint32_t it = atomicAdd(&ctrl->work, 1u);
+            s.items[cb ^ 1] = it;
+            s.bids[cb ^ 1] = it < nact ? act[it] : 0u;
+        }
+        float4 *gv = s.graw[cb];
+
+        // 1. grid operation of the 6^3 G2P region, in place (warps 1-7)
+        if (tid >= 32 && tid < 32 + 216) {
+            const int q = tid - 32;
+            const int i = 4 * bx + q % 6, j = 4 * by + (q / 6) % 6, k = 4 * bz + q / 36;
+            const float4 g = gv[q];
             float3 v = make_float3(0.f, 0.f, 0.f);
-            if (i < n && j < n && k < n) {
-                const float4 g = Gcur[node_addr(i, j, k, nb)];
-                v = grid_node_update(g.x, g.y, g.z, g.w, i, j, k, P, s.tools);
-            }
-            s.v[tid] = make_float4(v.x, v.y, v.z, 0.f);
+            if (i < n && j < n && k < n) v = grid_node_update(g.x, g.y, g.z, g.w, i, j, k, P, s.tools);
+            gv[q] = make_float4(v.x, v.y, v.z, 0.f);
         }
-        // runs heading to b: source lane l covers direction d = 26 - l, i.e.
-        // source block b - dir(d), in ascending source-block order
-        if (warp == 0) {
-            uint32_t np = 0, first = 0;
-            if (lane < 27) {
-                const int d = 26 - lane;
-                const int sx = bx - dir_dx(d), sy = by - dir_dy(d), sz = bz - dir_dz(d);
-                if (sx >= 0 && sy >= 0 && sz >= 0 && sx < nb && sy < nb && sz < nb) {
-                    const BlockTab t = tin[block_id(sx, sy, sz, nb)];
-                    if (t.stamp == step) { np = t.npass; first = t.first; }
-                }
-            }
-            uint32_t incl = np;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (lane < 27) { s.lane_first[lane] = first; s.lane_np[lane] = np; s.lane_off[lane] = incl - np; }
-            if (lane == 26) s.ncand = incl;
-        }
-        for (int q = tid; q < 2048; q += T) (&s.acc[0][0])[q] = 0.f;
+        for (int q = tid; q < 4 * kArena; q += T) (&s.acc[0][0])[q] = 0;
         for (int q = tid; q < 2 * NW * 28; q += T) (&s.wcnt[0][0][0])[q] = 0u;
-        __syncthreads();
-        uint32_t ncand = s.ncand;
-        if (ncand > CMAX) { ncand = CMAX; err |= kErrCapacity; }
-        for (uint32_t c = tid; c < ncand; c += T) {
-            int l = 0;
-            while (l < 26 && s.lane_off[l + 1] <= c) ++l;
-            const uint2 r = cin[s.lane_first[l] + (c - s.lane_off[l])].run[26 - l];
-            s.cand_start[c] = r.x;
-            s.cand_pre[c] = r.y;
-        }
-        __syncthreads();
-        // exclusive scan of run lengths (ncand <= 2 per thread)
-        {
-            const uint32_t c0 = 2 * tid, c1 = 2 * tid + 1;
-            const uint32_t l0 = c0 < ncand ? s.cand_pre[c0] : 0u, l1 = c1 < ncand ? s.cand_pre[c1] : 0u;
-            const uint32_t sum = l0 + l1;
-            uint32_t incl = sum;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+        // 2. warp 0: the runs heading to b, in ascending source-block order
+        //    (direction d = 26 .. 0, source pass 0 .. 3), with their exclusive
+        //    prefix = logical index of each run's first particle
+        if (warp == 0) {
+            const uint4 *ib = s.inbox[cb];
+            uint32_t nc = 0, carry = 0;
+            if (ib[kInbox - 1].x != step) {
+                for (int base = 0; base < 27 * kNpMax; base += 32) {
+                    const int idx = base + lane;
+                    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+                    if (idx < 27 * kNpMax) e = ib[(26 - (idx / kNpMax)) * kNpMax + (idx % kNpMax)];
+                    const bool ok = idx < 27 * kNpMax && e.z == step && e.y > 0u;
+                    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                    const uint32_t cnt = ok ? e.y : 0u;
+                    uint32_t incl = cnt;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    if (ok) {
+                        const uint32_t pos = nc + __popc(bal & ((1u << lane) - 1u));
+                        s.cand_start[pos] = e.x;
+                        s.cand_pre[pos] = carry + incl - cnt;
+                    }
+                    nc += __popc(bal);
+                    carry += __shfl_sync(0xffffffffu, incl, 31);
+                }
+            } else {
+                // a source wrote more passes than the inbox holds: walk its run tables
+                uint32_t np = 0, first = 0;
+                if (lane < 27) {
+                    const int d = 26 - lane;
+                    const int sx = bx - dir_dx(d), sy = by - dir_dy(d), sz = bz - dir_dz(d);
+                    if (sx >= 0 && sy >= 0 && sz >= 0 && sx < nb && sy < nb && sz < nb) {
+                        const BlockTab t = tin[block_id(sx, sy, sz, nb)];
+                        if (t.stamp == step) { np = t.npass; first = t.first; }
+                    }
+                }
+                uint32_t incl = np;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (lane < 27) { s.lane_first[lane] = first; s.lane_off[lane] = incl - np; }
+                uint32_t ncand = __shfl_sync(0xffffffffu, incl, 26);
+                if (ncand > CMAX) { ncand = CMAX; err |= kErrCapacity; }
+                __syncwarp();
+                for (uint32_t c0 = 0; c0 < ncand; c0 += 32) {
+                    const uint32_t c = c0 + lane;
+                    uint2 r = make_uint2(0u, 0u);
+                    if (c < ncand) {
+                        int l = 0;
+                        while (l < 26 && s.lane_off[l + 1] <= c) ++l;
+                        r = cin[s.lane_first[l] + (c - s.lane_off[l])].run[26 - l];
+                    }
+                    uint32_t incl2 = r.y;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl2, o);
+                        if (lane >= o) incl2 += y;
+                    }
+                    if (c < ncand) { s.cand_start[c] = r.x; s.cand_pre[c] = carry + incl2 - r.y; }
+                    carry += __shfl_sync(0xffffffffu, incl2, 31);
+                }
+                nc = ncand;
             }
-            __syncthreads();
-            if (lane == 31) s.wcnt[0][warp][0] = incl;
-            __syncthreads();
-            uint32_t wbase = 0, total = 0;
-            for (int w = 0; w < NW; ++w) {
-                const uint32_t x = s.wcnt[0][w][0];
-                if (w < warp) wbase += x;
-                total += x;
-            }
-            const uint32_t e0 = wbase + incl - sum;
-            __syncthreads();
-            if (c0 < ncand) s.cand_pre[c0] = e0;
-            if (c1 < ncand) s.cand_pre[c1] = e0 + l0;
-            if (tid == 0) {
-                s.cand_pre[ncand] = total;
+            __syncwarp();
+            if (lane == 0) {
+                s.ncand = nc;
+                s.cand_pre[nc] = carry;
+                const uint32_t total = carry;
                 s.total = total;
                 const uint32_t npass = (total + T - 1) / T;
-                uint32_t ob = atomicAdd(&ctrl->part_alloc, total);
-                uint32_t cf = atomicAdd(&ctrl->chunk_alloc, npass);
+                const uint32_t ob = atomicAdd(&ctrl->part_alloc, total);
+                const uint32_t cf = atomicAdd(&ctrl->chunk_alloc, npass);
+                BlockTab t;
+                t.pad = 0;
                 if (ob + total > nparticles || cf + npass > nchunk_cap) {
                     err |= kErrCapacity;
                     s.npass = 0;
-                    BlockTab t; t.stamp = 0; t.first = 0; t.npass = 0; t.pad = 0;
-                    tout[b] = t;
+                    t.stamp = 0; t.first = 0; t.npass = 0;
                 } else {
                     s.npass = npass;
-                    BlockTab t; t.stamp = step + 1; t.first = cf; t.npass = npass; t.pad = 0;
-                    tout[b] = t;
+                    t.stamp = step + 1; t.first = cf; t.npass = npass;
                 }
+                tout[b] = t;
                 s.out_base = ob;
                 s.chunk_first = cf;
                 s.mask = 0;
-                s.wcnt[0][0][0] = 0u;
-                for (int w = 1; w < NW; ++w) s.wcnt[0][w][0] = 0u;
+                s.bmax = 0;
             }
         }
         __syncthreads();
+        // start copying the next block's inputs; they land while this block computes
+        if (s.items[cb ^ 1] < nact) prefetch_block(s, cb ^ 1, s.bids[cb ^ 1], inbox_in, Gcur, nb, n, tid);
+        const uint32_t ncand = s.ncand;
         const uint32_t total = s.total, npass = s.npass, out_base = s.out_base, chunk_first = s.chunk_first;
         const int ox = 4 * bx - 1, oy = 4 * by - 1, oz = 4 * bz - 1;   // arena origin
 
         for (uint32_t pass = 0; pass < npass; ++pass) {
             const uint32_t j = pass * T + tid;
             const bool valid = j < total;
+            const int slot = (pass & 1) * T + tid;     // staging slot within the group
             int d = 31;
             float nxp = 0.f, nyp = 0.f, nzp = 0.f, idf = 0.f, Fn[9], Cm[9], vx = 0.f, vy = 0.f, vz = 0.f;
             if (valid) {
@@ -208,7 +299,7 @@ __global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, c
                 const float4 a0 = in.f0[src], a1 = in.f1[src];
                 const float F[9] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, in.f2[src]};
                 idf = xi.w;
-                // --- G2P from the shared velocities
+                // --- G2P from the shared velocities (Eqs. 8-9)
                 int gx, gy, gz;
                 const float fx = stencil_axis(xi.x, P.inv_dx, n, gx, err);
                 const float fy = stencil_axis(xi.y, P.inv_dx, n, gy, err);
@@ -228,7 +319,7 @@ __global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, c
 #pragma unroll
                     for (int jj = 0; jj < 3; ++jj) {
                         const float wjk = wy[jj] * wz[kk];
-                        const float4 *row = &s.v[lx + 6 * (ly + jj) + 36 * (lz + kk)];
+                        const float4 *row = &gv[lx + 6 * (ly + jj) + 36 * (lz + kk)];
                         float ax = 0.f, ay = 0.f, az = 0.f, bxx = 0.f, bxy = 0.f, bxz = 0.f;
 #pragma unroll
                         for (int ii = 0; ii < 3; ++ii) {
@@ -247,6 +338,7 @@ __global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, c
                 const float cs = 4.0f * P.inv_dx;
 #pragma unroll
                 for (int q = 0; q < 9; ++q) Cm[q] = cs * B9[q];
+                // --- Eq. 4 and Eq. 10
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -259,59 +351,51 @@ __global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, c
                     err |= kErrNumeric;
                     nxp = xi.x; nyp = xi.y; nzp = xi.z;
                 }
-                // --- stress of the new state and P2G into the arena
+                // --- stress of the new state (Eqs. 5-6) and the P2G inputs (Eqs. 1-3)
                 float t[6];
                 kirchhoff(Fn, P.mu, P.lam, t, err);
-                const float m = P.mass, kst = P.stress_k, dxs = P.dx;
-                const float A[9] = {(m * Cm[0] - kst * t[0]) * dxs, (m * Cm[1] - kst * t[1]) * dxs, (m * Cm[2] - kst * t[2]) * dxs,
-                                    (m * Cm[3] - kst * t[1]) * dxs, (m * Cm[4] - kst * t[3]) * dxs, (m * Cm[5] - kst * t[4]) * dxs,
-                                    (m * Cm[6] - kst * t[2]) * dxs, (m * Cm[7] - kst * t[4]) * dxs, (m * Cm[8] - kst * t[5]) * dxs};
+                const float kst = P.stress_k, dxs = P.dx;
+                float A[9] = {(m * Cm[0] - kst * t[0]) * dxs, (m * Cm[1] - kst * t[1]) * dxs, (m * Cm[2] - kst * t[2]) * dxs,
+                              (m * Cm[3] - kst * t[1]) * dxs, (m * Cm[4] - kst * t[3]) * dxs, (m * Cm[5] - kst * t[4]) * dxs,
+                              (m * Cm[6] - kst * t[2]) * dxs, (m * Cm[7] - kst * t[4]) * dxs, (m * Cm[8] - kst * t[5]) * dxs};
                 int hx, hy, hz;
                 const float ex = stencil_axis(nxp, P.inv_dx, n, hx, err);
                 const float ey = stencil_axis(nyp, P.inv_dx, n, hy, err);
                 const float ez = stencil_axis(nzp, P.inv_dx, n, hz, err);
-                bspline_weights(ex, wx);
-                bspline_weights(ey, wy);
-                bspline_weights(ez, wz);
+                // q = m v - A' fx: the value at stencil offset o is q + A' o
                 const float qx = m * vx - (A[0] * ex + A[1] * ey + A[2] * ez);
                 const float qy = m * vy - (A[3] * ex + A[4] * ey + A[5] * ez);
                 const float qz = m * vz - (A[6] * ex + A[7] * ey + A[8] * ez);
+                if (!(isfinite(qx) && isfinite(qy) && isfinite(qz))) err |= kErrNumeric;
                 const int ax0 = hx - ox, ay0 = hy - oy, az0 = hz - oz;
                 const bool in_arena = ax0 >= 0 && ax0 <= 5 && ay0 >= 0 && ay0 <= 5 && az0 >= 0 && az0 <= 5;
                 if (in_arena) {
-                    const int a0i = ax0 + 8 * ay0 + 64 * az0;
+                    s.st_base[slot] = ax0 + kAy * ay0 + kAz * az0;
+                    s.st_f[0][slot] = ex; s.st_f[1][slot] = ey; s.st_f[2][slot] = ez;
+                    s.st_q[0][slot] = qx; s.st_q[1][slot] = qy; s.st_q[2][slot] = qz;
 #pragma unroll
-                    for (int kk = 0; kk < 3; ++kk) {
-#pragma unroll
-                        for (int jj = 0; jj < 3; ++jj) {
-                            const float wjk = wy[jj] * wz[kk];
-                            const float rx = qx + A[1] * jj + A[2] * kk;
-                            const float ry = qy + A[4] * jj + A[5] * kk;
-                            const float rz = qz + A[7] * jj + A[8] * kk;
-#pragma unroll
-                            for (int ii = 0; ii < 3; ++ii) {
-                                const float w = wx[ii] * wjk;
-                                const int a = a0i + ii + 8 * jj + 64 * kk;
-                                atomicAdd(&s.acc[0][a], w * m);
-                                atomicAdd(&s.acc[1][a], w * (rx + A[0] * ii));
-                                atomicAdd(&s.acc[2][a], w * (ry + A[3] * ii));
-                                atomicAdd(&s.acc[3][a], w * (rz + A[6] * ii));
-                            }
-                        }
-                    }
+                    for (int q = 0; q < 9; ++q) s.st_a[q][slot] = A[q];
+                    // bound of |q + A' o| over the stencil, per component
+                    const float b0 = fabsf(qx) + 2.f * (fabsf(A[0]) + fabsf(A[1]) + fabsf(A[2]));
+                    const float b1 = fabsf(qy) + 2.f * (fabsf(A[3]) + fabsf(A[4]) + fabsf(A[5]));
+                    const float b2 = fabsf(qz) + 2.f * (fabsf(A[6]) + fabsf(A[7]) + fabsf(A[8]));
+                    const float bp = fmaxf(fmaxf(b0, b1), b2);
+                    atomicMax(&s.bmax, isfinite(bp) ? __float_as_uint(bp) : 0u);
                 } else {
                     // moved further than one cell: scatter straight into G_{k+1}
-#pragma unroll
+                    s.st_base[slot] = -1;
+                    float wx2[3], wy2[3], wz2[3];
+                    bspline_weights(ex, wx2);
+                    bspline_weights(ey, wy2);
+                    bspline_weights(ez, wz2);
                     for (int kk = 0; kk < 3; ++kk)
-#pragma unroll
                         for (int jj = 0; jj < 3; ++jj) {
-                            const float wjk = wy[jj] * wz[kk];
+                            const float wjk = wy2[jj] * wz2[kk];
                             const float rx = qx + A[1] * jj + A[2] * kk;
                             const float ry = qy + A[4] * jj + A[5] * kk;
                             const float rz = qz + A[7] * jj + A[8] * kk;
-#pragma unroll
                             for (int ii = 0; ii < 3; ++ii) {
-                                const float w = wx[ii] * wjk;
+                                const float w = wx2[ii] * wjk;
                                 atomicAdd(&Gnext[node_addr(hx + ii, hy + jj, hz + kk, nb)],
                                           make_float4(w * m, w * (rx + A[0] * ii), w * (ry + A[3] * ii), w * (rz + A[6] * ii)));
                             }
@@ -328,6 +412,8 @@ __global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, c
                     ddx = min(max(ddx, -1), 1); ddy = min(max(ddy, -1), 1); ddz = min(max(ddz, -1), 1);
                 }
                 d = (ddx + 1) + 3 * (ddy + 1) + 9 * (ddz + 1);
+            } else {
+                s.st_base[slot] = -1;
             }
             // --- stable rank by direction within the pass
             const unsigned peers = __match_any_sync(0xffffffffu, d);
@@ -353,6 +439,14 @@ __global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, c
                 if (lane < 27) {
                     s.dstart[lane] = incl - run;
                     cout[chunk_first + pass].run[lane] = make_uint2(pbase + incl - run, run);
+                    const int tx = bx + dir_dx(lane), ty = by + dir_dy(lane), tz = bz + dir_dz(lane);
+                    if (run > 0u && tx >= 0 && ty >= 0 && tz >= 0 && tx < nb && ty < nb && tz < nb) {
+                        uint4 *dst = inbox_out + (size_t)block_id(tx, ty, tz, nb) * kInbox;
+                        if (pass < (uint32_t)kNpMax)
+                            dst[lane * kNpMax + pass] = make_uint4(pbase + incl - run, run, step + 1, 0u);
+                        else
+                            dst[kInbox - 1] = make_uint4(step + 1, 0u, 0u, 0u);   // overflow: use the run tables
+                    }
                 }
                 const unsigned nz = __ballot_sync(0xffffffffu, lane < 27 && run > 0);
                 if (lane == 0) s.mask |= nz;
@@ -366,17 +460,70 @@ __global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, c
                 out.f2[pos] = Fn[8];
                 if (WRITE_VC) store_vc(B.vc, pos, vx, vy, vz, Cm);
             }
-        }
-        __syncthreads();
-        // 4. arena -> G_{k+1}
-        for (int q = tid; q < 512; q += T) {
-            const float am = s.acc[0][q], px = s.acc[1][q], py = s.acc[2][q], pz = s.acc[3][q];
-            if (am != 0.f || px != 0.f || py != 0.f || pz != 0.f) {
-                const int i = ox + (q & 7), jn = oy + ((q >> 3) & 7), k = oz + (q >> 6);
-                if (i >= 0 && jn >= 0 && k >= 0 && i < n && jn < n && k < n)
-                    atomicAdd(&Gnext[node_addr(i, jn, k, nb)], make_float4(am, px, py, pz));
+
+            // --- P2G of the staged group (after every second pass and the last one).
+            // Lane l of warp w scatters staged slot 2 l + (w & 1) + 64 (w >> 1):
+            // neighbouring lanes then hold particles of different cells.
+            if ((pass & 1) == 1 || pass + 1 == npass) {
+                const int nstaged = (int)min((uint32_t)GROUP, total - (pass & ~1u) * T);
+                const float bmax = __uint_as_float(s.bmax);
+                const float sv = bmax > 0.f ? kFix / bmax : 1.0f;   // momentum fixed-point scale
+                for (int q0 = tid; q0 < GROUP; q0 += T) {
+                    const int q = (q0 & ~255) + ((q0 & 31) * 2 + ((q0 >> 5) & 1)) + 64 * ((q0 & 255) >> 6);
+                    if (q >= nstaged) continue;
+                    const int base = s.st_base[q];
+                    if (base < 0) continue;
+                    float wx[3], wy[3], wz[3];
+                    bspline_weights(s.st_f[0][q], wx);
+                    bspline_weights(s.st_f[1][q], wy);
+                    bspline_weights(s.st_f[2][q], wz);
+                    float A[9];
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) A[c] = s.st_a[c][q];
+                    const float qx = s.st_q[0][q], qy = s.st_q[1][q], qz = s.st_q[2][q];
+#pragma unroll
+                    for (int kk = 0; kk < 3; ++kk) {
+#pragma unroll
+                        for (int jj = 0; jj < 3; ++jj) {
+                            const float wjk = wy[jj] * wz[kk];
+                            const float rx = qx + A[1] * jj + A[2] * kk;
+                            const float ry = qy + A[4] * jj + A[5] * kk;
+                            const float rz = qz + A[7] * jj + A[8] * kk;
+#pragma unroll
+                            for (int ii = 0; ii < 3; ++ii) {
+                                const float w = wx[ii] * wjk, ws = w * sv;
+                                const int a = base + ii + kAy * jj + kAz * kk;
+                                atomicAdd(&s.acc[0][a], fix_round(fmaf(w, kFix, kMagic)));
+                                atomicAdd(&s.acc[1][a], fix_round(fmaf(ws, rx + A[0] * ii, kMagic)));
+                                atomicAdd(&s.acc[2][a], fix_round(fmaf(ws, ry + A[3] * ii, kMagic)));
+                                atomicAdd(&s.acc[3][a], fix_round(fmaf(ws, rz + A[6] * ii, kMagic)));
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                // arena -> G_{k+1}, then reset it for the next group
+                const float um = m / kFix, up = 1.0f / sv;
+                for (int q = tid; q < 512; q += T) {
+                    const int lx8 = q & 7, ly8 = (q >> 3) & 7, lz8 = q >> 6;
+                    const int a = lx8 + kAy * ly8 + kAz * lz8;
+                    const int am = s.acc[0][a], px = s.acc[1][a], py = s.acc[2][a], pz = s.acc[3][a];
+                    if (am != 0 || px != 0 || py != 0 || pz != 0) {
+                        const int i = ox + lx8, jn = oy + ly8, k = oz + lz8;
+                        if (i >= 0 && jn >= 0 && k >= 0 && i < n && jn < n && k < n)
+                            atomicAdd(&Gnext[node_addr(i, jn, k, nb)],
+                                      make_float4((float)am * um, (float)px * up, (float)py * up, (float)pz * up));
+                        s.acc[0][a] = 0; s.acc[1][a] = 0; s.acc[2][a] = 0; s.acc[3][a] = 0;
+                    }
+                }
+                // every thread read s.bmax before the barrier above; the next
+                // group's atomicMax comes after the barrier below
+                if (tid == 0) s.bmax = 0;
+                __syncthreads();
             }
         }
+        cp_async_wait_all();
+        __syncthreads();
         // blocks of the next sub-step and grid blocks to clear before G_{k+1}'s reuse
         if (warp == 0 && lane < 27) {
             const int tx = bx + dir_dx(lane), ty = by + dir_dy(lane), tz = bz + dir_dz(lane);
@@ -412,20 +559,29 @@ __global__ void __launch_bounds__(T, 2) k_fused_step(DevParams P, FusedBufs B, c
     }
 }
 
+template <bool V>
+void set_smem_attr() {
+    cudaFuncSetAttribute(k_fused_step<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FusedSmem));
+}
+
 }  // namespace
 
 void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, bool write_vc, int grid,
                        cudaStream_t st) {
     if (write_vc)
-        k_fused_step<true><<<grid, T, 0, st>>>(P, B, tools);
+        k_fused_step<true><<<grid, T, sizeof(FusedSmem), st>>>(P, B, tools);
     else
-        k_fused_step<false><<<grid, T, 0, st>>>(P, B, tools);
+        k_fused_step<false><<<grid, T, sizeof(FusedSmem), st>>>(P, B, tools);
 }
 
+// Also opts the kernel into its dynamic shared memory size on the current
+// device; called when a handle is created.
 int fused_step_occupancy(int threads) {
+    set_smem_attr<true>();
+    set_smem_attr<false>();
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fused_step<true>, threads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_step<false>, threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fused_step<true>, threads, sizeof(FusedSmem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_step<false>, threads, sizeof(FusedSmem));
     return a < b ? a : b;
 }
 

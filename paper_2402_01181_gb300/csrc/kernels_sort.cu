@@ -197,6 +197,7 @@ __global__ void k_init_tables(DevParams P, const uint32_t *__restrict__ offsets,
         B.tabs[par][b] = t;
         Chunk &ch = B.chunks[par][b];
         for (int d = 0; d < 27; ++d) ch.run[d] = make_uint2(d == 13 ? off : 0u, d == 13 ? c : 0u);
+        B.inbox[par][(size_t)b * kInbox + 13 * kNpMax] = make_uint4(off, c, step, 0u);
         B.astamp[b] = step;
         B.alist[par][atomicAdd(&B.ctrl->nactive[par], 1u)] = b;
         const int bx = b % P.nb, by = (b / P.nb) % P.nb, bz = b / (P.nb * P.nb);

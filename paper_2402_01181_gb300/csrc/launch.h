@@ -53,6 +53,7 @@ struct FusedBufs {
     uint32_t *alist[2];       // active blocks by sub-step parity
     uint32_t *clist[3];       // grid blocks to clear, by sub-step mod 3
     float4 *G[3];             // grid buffers by sub-step mod 3
+    uint4 *inbox[2];          // per destination block: kInbox entries (first slot, count, stamp, 0)
     uint32_t *astamp;         // per block: last sub-step it was put on an active list
     uint32_t *gstamp;         // per block: last sub-step it was put on a clear list
     Ctrl *ctrl;
@@ -62,5 +63,10 @@ void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *
                        cudaStream_t st);
 int fused_step_occupancy(int threads);
 constexpr int kFusedThreads = 256;
+// Inbox of a block: entry d * kNpMax + p holds the run of source pass p
+// coming from direction d (source block = block - dir(d)); the last entry,
+// stamped, says that some source had more than kNpMax passes.
+constexpr int kNpMax = 4;
+constexpr int kInbox = 27 * kNpMax + 1;
 
 }  // namespace gbmpm
