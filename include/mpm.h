@@ -171,6 +171,33 @@ mpm_status mpm_grid_velocity(mpm_handle *h, float *v, int on_device);
  * (clamped to the grid).  Host arrays of n entries.  Synchronises. */
 mpm_status mpm_read_order(mpm_handle *h, uint32_t *ids, uint32_t *keys);
 
+/* ------------------------------------------------------ without allocation */
+
+/* The stable block sort that mpm_load_particles performs, for callers that
+ * must not allocate device memory: code running inside a host that owns all
+ * of the GPU's memory through its own pool or a fixed budget, where a
+ * cudaMalloc (or a framework allocator call) would fail or is not allowed.
+ * The paper has no counterpart; this is a utility of this library.
+ *
+ * x: n x 3 particle positions in device memory.  ids, keys: device outputs of
+ * n entries: the particle indices sorted by the block key of
+ * floor(x/dx - 0.5) (dx = 1/n_grid, clamped to the grid), ties in index
+ * order, and each entry's key bx + nb*(by + nb*bz), nb = n_grid/4 -- the same
+ * result as mpm_read_order after mpm_load_particles.  n_grid: a power of two
+ * in [8, 256]; n <= 2^30; larger sizes return MPM_ERR_ARG.
+ *
+ * Allocates nothing: its scratch is one static device array of about 3 MB
+ * that every GPU using the library holds until the process exits.  The first
+ * call on a device looks up that array's address (cudaGetSymbolAddress, with
+ * the device current), so make it before any stream capture.  Every call
+ * shares the array and leaves its contents behind (the counters are cleared
+ * at the start of each call); calls that overlap on the GPU, on any streams,
+ * race and must not be issued.  Runs on cuda_stream (NULL = legacy default)
+ * and synchronises it; returns MPM_ERR_NUMERIC / MPM_ERR_DOMAIN for
+ * non-finite or clamped positions. */
+mpm_status mpm_block_sort_noalloc(const float *x, int64_t n, int32_t n_grid, uint32_t *ids,
+                                  uint32_t *keys, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,10 @@ struct Alloc {
 
 }  // namespace
 
+namespace gbmpm {
+void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+}  // namespace gbmpm
+
 struct mpm_handle {
     mpm_config cfg{};
     DevParams P{};

@@ -8,6 +8,9 @@
 
 namespace gbmpm {
 
+// capi.cu: the message mpm_last_error() returns on this thread
+void set_last_error(const char *msg);
+
 // kernels_split.cu
 void launch_p2g_scatter(const DevParams &P, const PState &S, const VCState &V, uint32_t n, float4 *G, Ctrl *ctrl,
                         int grid, cudaStream_t st);

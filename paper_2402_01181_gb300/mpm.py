@@ -72,6 +72,8 @@ SIGNATURES = [
     ("mpm_read_grid", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int]),
     ("mpm_grid_velocity", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_int]),
     ("mpm_read_order", ct.c_int, [ct.c_void_p, _U32P, _U32P]),
+    ("mpm_block_sort_noalloc", ct.c_int, [ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_void_p, ct.c_void_p,
+                                          ct.c_void_p]),
 ]
 
 
@@ -104,6 +106,7 @@ mpm_set_stream = lib.mpm_set_stream
 mpm_read_grid = lib.mpm_read_grid
 mpm_grid_velocity = lib.mpm_grid_velocity
 mpm_read_order = lib.mpm_read_order
+mpm_block_sort_noalloc = lib.mpm_block_sort_noalloc
 
 
 def mpm_last_error() -> str:
