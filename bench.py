@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--pipeline", default="fused", choices=["fused", "split"])
     ap.add_argument("--no-secondary", action="store_true", help="skip the 30K slab line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-environment measurement")
+    ap.add_argument("--batch-envs", type=int, default=256)
     return ap.parse_args()
 
 
@@ -200,6 +202,97 @@ def run_gpu_workload(name, args, rank, device, barrier, max_over_ranks, with_e2e
     return res
 
 
+def run_batched(args, rank, device, barrier, max_over_ranks, steps=6, loop_steps=2):
+    """Batched environments (SURVEY config 4): n_envs independent slab scenes
+    of 5K-40K particles on their own 64^3 grids, stepped by one handle (one
+    fused launch per sub-step over all environments), against the per-env
+    loop of n_envs single-environment handles on the same GPU.  Metric:
+    env-steps/s = environments x sub-steps / time."""
+    import torch
+    from paper_2402_01181_gb300 import dist as D
+    from paper_2402_01181_gb300 import mpm
+    S = args.substeps
+    envs = scenes.batch_envs(args.batch_envs, seed=D.replica_seed(rank))
+    ne = len(envs)
+    total = sum(e.n for e in envs)
+    stream = torch.cuda.current_stream(device)
+    cfg = mpm.make_config(64, envs[0].dt, 1e4, 0.3, 1e3, friction=0.3, n_envs=ne, max_particles=total)
+    sim = mpm.Sim(cfg)
+    for i, sc in enumerate(envs):
+        sim.set_env_material(i, sc.E, sc.nu, sc.rho)
+    sim.load_batch([sc.x for sc in envs], [sc.particle_volume for sc in envs])
+    for i, sc in enumerate(envs):
+        sim.set_env_tool(i, 0, sc.tools[0].pose(-1), sc.tools[0].shape)
+    s_next = [0]
+
+    def set_tools():
+        s = s_next[0]
+        for i, sc in enumerate(envs):
+            sim.set_env_tool(i, 0, sc.tools[0].pose(s + S - 1), sc.tools[0].shape)
+        s_next[0] = s + S
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    for _ in range(args.warmup):
+        set_tools()
+        sim.step(S)
+    sim.synchronize()
+    barrier()
+    ms = 0.0
+    for _ in range(steps):
+        set_tools()
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(S)
+        b.record(stream)
+        torch.cuda.synchronize(device)
+        ms += a.elapsed_time(b)
+    if sim.status() != mpm.MPM_OK:
+        raise RuntimeError("device error in the batched run: %s" % mpm.mpm_last_error())
+    sim.close()
+    t_batched = max_over_ranks(ms)
+    # the per-env loop: one handle per environment, stepped one after another
+    sims = []
+    for sc in envs:
+        c1 = mpm.make_config(64, sc.dt, sc.E, sc.nu, sc.rho, friction=0.3, max_particles=sc.n)
+        si = mpm.Sim(c1)
+        si.load(sc.x, sc.particle_volume)
+        si.set_tool(0, sc.tools[0].pose(-1), sc.tools[0].shape)
+        sims.append(si)
+    s_loop = [0]
+
+    def loop_frame():
+        s = s_loop[0]
+        for si, sc in zip(sims, envs):
+            si.set_tool(0, sc.tools[0].pose(s + S - 1), sc.tools[0].shape)
+            si.step(S)
+        s_loop[0] = s + S
+
+    loop_frame()
+    torch.cuda.synchronize(device)
+    barrier()
+    ms_loop = 0.0
+    for _ in range(loop_steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        loop_frame()
+        b.record(stream)
+        torch.cuda.synchronize(device)
+        ms_loop += a.elapsed_time(b)
+    for si in sims:
+        si.close()
+    t_loop = max_over_ranks(ms_loop)
+    world = D.env()[0]
+    env_steps = ne * S * steps * world / (t_batched / 1e3)
+    loop_env_steps = ne * S * loop_steps * world / (t_loop / 1e3)
+    return {"workload": "batch%d" % ne, "n_envs": ne, "particles": total, "n_grid": 64,
+            "env_steps_per_s": env_steps, "particle_steps_per_s": total * S * steps * world / (t_batched / 1e3),
+            "ms_per_step": t_batched / steps, "loop_env_steps_per_s": loop_env_steps,
+            "loop_ms_per_step": t_loop / loop_steps, "speedup_vs_loop": env_steps / loop_env_steps,
+            "gpu_launches_per_step": S}
+
+
 def algorithmic_bytes_per_particle_step(n, active_nodes, S):
     """Minimum DRAM traffic of one fused sub-step, per particle: the particle
     state is read and written once (x, id: 16 B; F: 36 B; twice = 104 B); each
@@ -293,6 +386,10 @@ def main():
                   "ms_per_step": r2["t_ms"] / r2["steps"],
                   "e2e": r2["n"] * S * r2["steps"] * world / (r2["t_e2e_ms"] / 1e3)}
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, rank, device, barrier, max_over_ranks)
+
     if rank != 0:
         ranks.close()
         return
@@ -333,6 +430,7 @@ def main():
         "gpu_launches": launches_per_frame * args.steps,
         "clocks": main_res["clocks"],
         "secondary": second,
+        "batched": batched,
     }
     print(json.dumps(line))
     ranks.close()

@@ -75,7 +75,11 @@ typedef struct mpm_config {
     float theta;            /* contact threshold: a node collides if its distance < theta */
     float friction_mu;      /* Coulomb coefficient of Eq. 18, >= 0 */
     int32_t pipeline;       /* MPM_PIPELINE_FUSED or MPM_PIPELINE_SPLIT */
-    int64_t max_particles;  /* capacity of the handle, >= 1 */
+    int32_t n_envs;         /* independent environments stepped together (0 or 1: one); more
+                               than one needs the fused pipeline.  All share n_grid, dt,
+                               gravity, bound, theta and friction_mu; each has its own particles,
+                               material (mpm_set_env_material) and tools (mpm_set_env_tool_pose) */
+    int64_t max_particles;  /* capacity of the handle over all environments, >= 1 */
 } mpm_config;
 
 /* Optional device allocator.  alloc returns a device pointer of at least
@@ -95,7 +99,8 @@ mpm_status mpm_destroy(mpm_handle *h);
 
 /* Replace the particle state with n particles (0 <= n <= max_particles).
  * x: n x 3 positions (required); v: n x 3 or NULL (zero); F: n x 9 or NULL
- * (identity); C: n x 9 or NULL (zero).  particle_volume: V_p^0 (> 0), the
+ * (identity); C: n x 9 or NULL (zero).  Handles with one environment only
+ * (see mpm_load_batch).  particle_volume: V_p^0 (> 0), the
  * same for every particle (Table I).  on_device != 0: the pointers are device
  * memory readable on the handle's stream; otherwise host memory.  The stored
  * F is taken as already updated by Eq. 4, so the first P2G uses P(F) F^T of
@@ -103,6 +108,27 @@ mpm_status mpm_destroy(mpm_handle *h);
 mpm_status mpm_load_particles(mpm_handle *h, int64_t n, const float *x, const float *v,
                               const float *F, const float *C, float particle_volume,
                               int on_device);
+
+/* Load every environment of a handle at once: counts[e] particles of
+ * environment e (e < n_envs), stored one environment after the other in x,
+ * v, F, C (layouts as for mpm_load_particles, NULL v/F/C as there);
+ * particle_volumes[e] is V_p^0 of environment e.  counts and
+ * particle_volumes are host arrays of n_envs entries.  Particle indices of
+ * every output run over the environments in this order. */
+mpm_status mpm_load_batch(mpm_handle *h, const int64_t *counts, const float *x, const float *v,
+                          const float *F, const float *C, const float *particle_volumes,
+                          int on_device);
+
+/* Material of environment env: Young's modulus, Poisson's ratio (Eq. 6) and
+ * density (mass = rho * particle volume).  Environments start with the
+ * values of mpm_config.  A change applies from the next stress evaluation;
+ * the grid already scattered keeps the previous values. */
+mpm_status mpm_set_env_material(mpm_handle *h, int32_t env, float E, float nu, float rho);
+
+/* mpm_set_tool_pose for environment env (mpm_set_tool_pose addresses
+ * environment 0). */
+mpm_status mpm_set_env_tool_pose(mpm_handle *h, int32_t env, int32_t tool_id, const double pose[6],
+                                 const float shape[8]);
 
 /* Set rigid tool tool_id (0 <= tool_id < MPM_MAX_TOOLS) (Sec. III-C).
  * pose: world translation T (3) then rotation vector (3): a reference-frame
@@ -154,13 +180,13 @@ mpm_status mpm_clear_error(mpm_handle *h);
 mpm_status mpm_set_stream(mpm_handle *h, void *cuda_stream);
 
 /* Grid mass and momentum that the next sub-step's grid operation starts from
- * (the P2G of the current particle state, Eqs. 1-2): n_grid^3 x 4 floats
- * (m, mv_x, mv_y, mv_z) per node.  Synchronises. */
+ * (the P2G of the current particle state, Eqs. 1-2): n_envs x n_grid^3 x 4
+ * floats (m, mv_x, mv_y, mv_z) per node, environment-major.  Synchronises. */
 mpm_status mpm_read_grid(mpm_handle *h, float *grid, int on_device);
 
 /* Grid velocities after the grid operation (Eq. 7, gravity, tools, walls)
  * applied to mpm_read_grid's state with the tool poses a following
- * mpm_step(h, 1) would use: n_grid^3 x 3 floats.  Synchronises. */
+ * mpm_step(h, 1) would use: n_envs x n_grid^3 x 3 floats.  Synchronises. */
 mpm_status mpm_grid_velocity(mpm_handle *h, float *v, int on_device);
 
 /* Fused pipeline only: the current order of the particles, i.e. the result
@@ -168,7 +194,8 @@ mpm_status mpm_grid_velocity(mpm_handle *h, float *v, int on_device);
  * order) sorted by grid-block key, ties in the order of the previous sort
  * (after a load: by particle index); keys: the block key of each entry,
  * bx + nb*(by + nb*bz) with nb = n_grid/4 and b = floor(x/dx - 0.5)/4
- * (clamped to the grid).  Host arrays of n entries.  Synchronises. */
+ * (clamped to the grid), plus e * nb^3 for a particle of environment e.
+ * Host arrays of n entries.  Synchronises. */
 mpm_status mpm_read_order(mpm_handle *h, uint32_t *ids, uint32_t *keys);
 
 /* ------------------------------------------------------ without allocation */

@@ -39,7 +39,6 @@ mpm_status fail(mpm_status st, const char *fmt, ...) {
         if (e_ != cudaSuccess) return fail(MPM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-constexpr int kMaxSubChunk = 512;   // sub-steps per captured graph / tool table
 
 // ------------------------------------------------------------ rotations
 
@@ -102,7 +101,11 @@ struct mpm_handle {
     void *alloc_ctx = nullptr;
     std::vector<Alloc> allocs;
     int device = 0, num_sms = 0, fused_grid = 0, elem_grid = 0;
-    uint32_t nblocks = 0, chunk_cap = 0;
+    int n_envs = 1;
+    int sub_chunk = 512;        // sub-steps per captured graph / frame upload
+    int tstride = 0;            // tool frames per environment in the uploaded table
+    uint32_t nbe = 0;           // blocks per environment
+    uint32_t nblocks = 0, chunk_cap = 0;   // over all environments
     int64_t n = 0;
     bool loaded = false;
     uint32_t step = 0;          // fused: device sub-step index mirrored on the host
@@ -118,7 +121,14 @@ struct mpm_handle {
     uint32_t *h_err = nullptr;       // pinned copy of Ctrl::err
     cudaEvent_t ev_err = nullptr, ev_frames = nullptr;
     bool err_pending = false;
-    HostTool tools[MPM_MAX_TOOLS];
+    std::vector<HostTool> tools;         // n_envs x MPM_MAX_TOOLS
+    // per-environment material
+    std::vector<double> env_E, env_nu, env_rho, env_vol;
+    std::vector<EnvParams> envp_host;
+    std::vector<uint32_t> env_off;       // n_envs + 1 particle offsets
+    EnvParams *d_envp = nullptr;
+    uint32_t *d_env_off = nullptr;
+    bool envp_dirty = true;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     bool use_graphs = true;
 };
@@ -186,56 +196,91 @@ int cur_m3(const mpm_handle *h) { return (int)(h->step % 3u); }
 
 const PState &cur_state(const mpm_handle *h) { return is_fused(h) ? h->fb.P[cur_par(h)] : h->fb.P[0]; }
 
+// Highest active tool slot + 1 over all environments.
+int tool_stride(const mpm_handle *h) {
+    int ts = 0;
+    for (int e = 0; e < h->n_envs; ++e)
+        for (int t = 0; t < MPM_MAX_TOOLS; ++t)
+            if (h->tools[(size_t)e * MPM_MAX_TOOLS + t].kind != MPM_TOOL_NONE) ts = std::max(ts, t + 1);
+    return ts;
+}
+
 // Tool frames of nsub sub-steps of a call that moves every tool from its
 // current pose to its target uniformly over `total` sub-steps, starting at
-// sub-step `first` of the call.
-int fill_frames(mpm_handle *h, int first, int nsub, int total, ToolFrame *out) {
-    int ntools = 0;
-    for (int t = 0; t < MPM_MAX_TOOLS; ++t)
-        if (h->tools[t].kind != MPM_TOOL_NONE) ntools = t + 1;
+// sub-step `first` of the call.  Layout: [sub-step][environment][tool slot],
+// tstride slots per environment.
+void fill_frames(mpm_handle *h, int first, int nsub, int total, int tstride, ToolFrame *out) {
     const double span = (double)total * (double)h->cfg.dt;
-    for (int t = 0; t < ntools; ++t) {
-        const HostTool &tl = h->tools[t];
-        const Quat q0 = qexp_rotvec(tl.cur + 3), q1 = qexp_rotvec(tl.tgt + 3);
-        const Quat dq = qmul(q1, Quat{q0.w, -q0.x, -q0.y, -q0.z});
-        double phi[3];
-        qlog_rotvec(dq, phi);
-        double reach = tl.kind == MPM_TOOL_CAPSULE ? tl.dims[0] + tl.dims[1]
-                                                   : std::sqrt(tl.dims[0] * tl.dims[0] + tl.dims[1] * tl.dims[1] +
-                                                               tl.dims[2] * tl.dims[2]);
-        reach += std::max(0.0, (double)h->cfg.theta);
-        reach = reach * 1.001 + 1e-6;
-        for (int k = 0; k < nsub; ++k) {
-            const double s = (double)(first + k + 1) / (double)total;
-            ToolFrame &f = out[k * MPM_MAX_TOOLS + t];
-            std::memset(&f, 0, sizeof f);
-            f.kind = tl.kind;
-            if (tl.kind == MPM_TOOL_NONE) continue;
-            const double rs[3] = {s * phi[0], s * phi[1], s * phi[2]};
-            double R[9];
-            qmatrix(qmul(qexp_rotvec(rs), q0), R);
-            for (int i = 0; i < 9; ++i) f.R[i] = (float)R[i];
-            for (int a = 0; a < 3; ++a) {
-                f.T[a] = (float)(tl.cur[a] + s * (tl.tgt[a] - tl.cur[a]));
-                f.u[a] = (float)((tl.tgt[a] - tl.cur[a]) / span);
-                f.w[a] = (float)(phi[a] / span);
-                f.dims[a] = (float)tl.dims[a];
+    for (int e = 0; e < h->n_envs; ++e)
+        for (int t = 0; t < tstride; ++t) {
+            const HostTool &tl = h->tools[(size_t)e * MPM_MAX_TOOLS + t];
+            const Quat q0 = qexp_rotvec(tl.cur + 3), q1 = qexp_rotvec(tl.tgt + 3);
+            const Quat dq = qmul(q1, Quat{q0.w, -q0.x, -q0.y, -q0.z});
+            double phi[3];
+            qlog_rotvec(dq, phi);
+            double reach = tl.kind == MPM_TOOL_CAPSULE ? tl.dims[0] + tl.dims[1]
+                                                       : std::sqrt(tl.dims[0] * tl.dims[0] + tl.dims[1] * tl.dims[1] +
+                                                                   tl.dims[2] * tl.dims[2]);
+            reach += std::max(0.0, (double)h->cfg.theta);
+            reach = reach * 1.001 + 1e-6;
+            for (int k = 0; k < nsub; ++k) {
+                const double s = (double)(first + k + 1) / (double)total;
+                ToolFrame &f = out[((size_t)k * h->n_envs + e) * tstride + t];
+                std::memset(&f, 0, sizeof f);
+                f.kind = tl.kind;
+                if (tl.kind == MPM_TOOL_NONE) continue;
+                const double rs[3] = {s * phi[0], s * phi[1], s * phi[2]};
+                double R[9];
+                qmatrix(qmul(qexp_rotvec(rs), q0), R);
+                for (int i = 0; i < 9; ++i) f.R[i] = (float)R[i];
+                for (int a = 0; a < 3; ++a) {
+                    f.T[a] = (float)(tl.cur[a] + s * (tl.tgt[a] - tl.cur[a]));
+                    f.u[a] = (float)((tl.tgt[a] - tl.cur[a]) / span);
+                    f.w[a] = (float)(phi[a] / span);
+                    f.dims[a] = (float)tl.dims[a];
+                }
+                f.reach2 = (float)(reach * reach);
             }
-            f.reach2 = (float)(reach * reach);
         }
+}
+
+// Per-environment material table and tool counts to the device (when changed).
+mpm_status upload_env_params(mpm_handle *h) {
+    const int ts = tool_stride(h);
+    for (int e = 0; e < h->n_envs; ++e) {
+        int nt = 0;
+        for (int t = 0; t < MPM_MAX_TOOLS; ++t)
+            if (h->tools[(size_t)e * MPM_MAX_TOOLS + t].kind != MPM_TOOL_NONE) nt = t + 1;
+        EnvParams &ep = h->envp_host[e];
+        const double E = h->env_E[e], nu = h->env_nu[e];   // Eq. 6
+        ep.mu = (float)(E / (2.0 * (1.0 + nu)));
+        ep.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
+        ep.mass = (float)(h->env_rho[e] * h->env_vol[e]);
+        ep.stress_k = (float)((double)h->cfg.dt * h->env_vol[e] * 4.0 * (double)h->P.inv_dx * h->P.inv_dx);
+        ep.ntools = std::min(nt, ts);
     }
-    return ntools;
+    if (ts != h->tstride || h->envp_dirty) {
+        CK(cudaStreamSynchronize(h->stream));   // no kernel still reads the old table
+        CK(cudaMemcpy(h->d_envp, h->envp_host.data(), sizeof(EnvParams) * h->n_envs, cudaMemcpyHostToDevice));
+        h->envp_dirty = false;
+    }
+    h->tstride = ts;
+    h->P.tstride = ts;
+    return MPM_OK;
 }
 
 // Upload frames for sub-steps [first, first+nsub) of a call of `total`.
 mpm_status upload_frames(mpm_handle *h, int first, int nsub, int total) {
+    // tool counts can change between calls: refresh the environment table
+    mpm_status st = upload_env_params(h);
+    if (st != MPM_OK) return st;
     // the pinned staging buffer may still feed an earlier copy
     CK(cudaEventSynchronize(h->ev_frames));
-    const int ntools = fill_frames(h, first, nsub, total, h->h_frames);
-    h->P.ntools = ntools;
-    if (ntools > 0)
-        CK(cudaMemcpyAsync(h->d_frames, h->h_frames, sizeof(ToolFrame) * MPM_MAX_TOOLS * nsub, cudaMemcpyHostToDevice,
-                           h->stream));
+    if (h->tstride > 0) {
+        fill_frames(h, first, nsub, total, h->tstride, h->h_frames);
+        CK(cudaMemcpyAsync(h->d_frames, h->h_frames, sizeof(ToolFrame) * (size_t)nsub * h->n_envs * h->tstride,
+                           cudaMemcpyHostToDevice, h->stream));
+    }
     CK(cudaEventRecord(h->ev_frames, h->stream));
     return MPM_OK;
 }
@@ -260,12 +305,11 @@ mpm_status enqueue_error_copy(mpm_handle *h) {
 }
 
 // Issue nsub sub-steps on stream st (used directly and under capture).
-mpm_status issue_substeps(mpm_handle *h, int nsub, bool write_vc_last, cudaStream_t st, int ntools) {
-    DevParams P = h->P;
-    P.ntools = ntools;
+mpm_status issue_substeps(mpm_handle *h, int nsub, bool write_vc_last, cudaStream_t st) {
+    const DevParams P = h->P;
     const uint32_t n = (uint32_t)h->n;
     for (int k = 0; k < nsub; ++k) {
-        const ToolFrame *fr = h->d_frames + (size_t)k * MPM_MAX_TOOLS;
+        const ToolFrame *fr = h->d_frames + (size_t)k * h->n_envs * h->tstride;
         const bool vc = write_vc_last && k == nsub - 1;
         if (is_fused(h)) {
             launch_fused_step(P, h->fb, fr, vc, h->fused_grid, st);
@@ -280,15 +324,15 @@ mpm_status issue_substeps(mpm_handle *h, int nsub, bool write_vc_last, cudaStrea
     return MPM_OK;
 }
 
-mpm_status run_chunk(mpm_handle *h, int nsub, bool write_vc_last, int ntools) {
-    if (!h->use_graphs) return issue_substeps(h, nsub, write_vc_last, h->stream, ntools);
-    // graphs are keyed by length, the vc flag and the number of tool slots
-    const std::pair<int, int> key(nsub, (write_vc_last ? 1 : 0) | (ntools << 1));
+mpm_status run_chunk(mpm_handle *h, int nsub, bool write_vc_last) {
+    if (!h->use_graphs) return issue_substeps(h, nsub, write_vc_last, h->stream);
+    // graphs are keyed by length, the vc flag and the tool-frame stride
+    const std::pair<int, int> key(nsub, (write_vc_last ? 1 : 0) | (h->tstride << 1));
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-        mpm_status st = issue_substeps(h, nsub, write_vc_last, h->cap_stream, ntools);
+        mpm_status st = issue_substeps(h, nsub, write_vc_last, h->cap_stream);
         cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
         if (st != MPM_OK) {
             if (g) cudaGraphDestroy(g);
@@ -339,6 +383,12 @@ mpm_status mpm_create(const mpm_config *cfg, void *cuda_stream, mpm_alloc_fn all
         return fail(MPM_ERR_ARG, "unknown pipeline %d", cfg->pipeline);
     if (cfg->max_particles < 1 || cfg->max_particles > (int64_t)1 << 30)
         return fail(MPM_ERR_ARG, "max_particles must be in [1, 2^30]");
+    const int n_envs = cfg->n_envs < 1 ? 1 : cfg->n_envs;
+    if (n_envs > 65536) return fail(MPM_ERR_ARG, "n_envs must be at most 65536");
+    if (n_envs > 1 && cfg->pipeline != MPM_PIPELINE_FUSED)
+        return fail(MPM_ERR_ARG, "several environments need the fused pipeline");
+    if ((uint64_t)n_envs * (uint64_t)(n / 4) * (n / 4) * (n / 4) > (1ull << 26))
+        return fail(MPM_ERR_ARG, "n_envs * (n_grid/4)^3 grid blocks exceed 2^26");
     if ((alloc == nullptr) != (free_fn == nullptr)) return fail(MPM_ERR_ARG, "alloc and free callbacks go together");
 
     mpm_handle *h = new (std::nothrow) mpm_handle();
@@ -361,28 +411,35 @@ mpm_status mpm_create(const mpm_config *cfg, void *cuda_stream, mpm_alloc_fn all
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return bail(fail(MPM_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e)));
 
+    h->n_envs = n_envs;
+    h->tools.assign((size_t)n_envs * MPM_MAX_TOOLS, HostTool());
+    h->env_E.assign(n_envs, cfg->E);
+    h->env_nu.assign(n_envs, cfg->nu);
+    h->env_rho.assign(n_envs, cfg->rho);
+    h->env_vol.assign(n_envs, 0.0);
+    h->envp_host.assign(n_envs, EnvParams{});
+    h->env_off.assign(n_envs + 1, 0u);
+    h->sub_chunk = std::max(1, std::min(512, 16384 / n_envs));
     DevParams &P = h->P;
     P.n = n;
     P.nb = n / 4;
+    P.nbe = (uint32_t)(P.nb * P.nb * P.nb);
+    P.n_envs = n_envs;
     P.bound = cfg->bound;
-    P.ntools = 0;
+    P.tstride = 0;
     P.dx = 1.0f / (float)n;
     P.inv_dx = (float)n;
     P.dt = cfg->dt;
     P.gx = cfg->gravity[0];
     P.gy = cfg->gravity[1];
     P.gz = cfg->gravity[2];
-    P.mass = 0.f;
-    const double E = cfg->E, nu = cfg->nu;   // Eq. 6
-    P.mu = (float)(E / (2.0 * (1.0 + nu)));
-    P.lam = (float)(E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)));
-    P.stress_k = 0.f;
     P.theta = cfg->theta;
     P.fric = cfg->friction_mu;
 
     const size_t N = (size_t)cfg->max_particles;
-    const size_t nn = (size_t)n * n * n;
-    h->nblocks = (uint32_t)(P.nb * P.nb * P.nb);
+    const size_t nn = (size_t)n * n * n * n_envs;   // grid nodes over all environments
+    h->nbe = P.nbe;
+    h->nblocks = P.nbe * (uint32_t)n_envs;
     h->chunk_cap = h->nblocks + (uint32_t)(N / kFusedThreads) + 1;
     h->fb.nblocks = h->nblocks;
     h->elem_grid = h->num_sms * 8;
@@ -407,7 +464,11 @@ mpm_status mpm_create(const mpm_config *cfg, void *cuda_stream, mpm_alloc_fn all
     for (int g = ngrid; g < 3; ++g) h->fb.G[g] = h->fb.G[0];
     if ((st = dalloc_t(h, &h->fb.ctrl, 1)) != MPM_OK) return bail(st);
     if ((st = dalloc_t(h, &h->staging, 24 * N)) != MPM_OK) return bail(st);
-    if ((st = dalloc_t(h, &h->d_frames, (size_t)kMaxSubChunk * MPM_MAX_TOOLS)) != MPM_OK) return bail(st);
+    if ((st = dalloc_t(h, &h->d_frames, (size_t)h->sub_chunk * n_envs * MPM_MAX_TOOLS)) != MPM_OK) return bail(st);
+    if ((st = dalloc_t(h, &h->d_envp, (size_t)n_envs)) != MPM_OK) return bail(st);
+    if ((st = dalloc_t(h, &h->d_env_off, (size_t)n_envs + 1)) != MPM_OK) return bail(st);
+    P.envp = h->d_envp;
+    P.env_off = h->d_env_off;
     if (cfg->pipeline == MPM_PIPELINE_FUSED) {
         for (int b = 0; b < 2; ++b) {
             if ((st = dalloc_t(h, &h->fb.chunks[b], h->chunk_cap)) != MPM_OK) return bail(st);
@@ -425,7 +486,7 @@ mpm_status mpm_create(const mpm_config *cfg, void *cuda_stream, mpm_alloc_fn all
         if ((st = dalloc_t(h, &h->sort.offsets, h->nblocks + 1)) != MPM_OK) return bail(st);
         if ((st = dalloc_t(h, &h->sort.cursor, h->nblocks)) != MPM_OK) return bail(st);
     }
-    e = cudaMallocHost(&h->h_frames, sizeof(ToolFrame) * kMaxSubChunk * MPM_MAX_TOOLS);
+    e = cudaMallocHost(&h->h_frames, sizeof(ToolFrame) * (size_t)h->sub_chunk * n_envs * MPM_MAX_TOOLS);
     if (e != cudaSuccess) return bail(fail(MPM_ERR_ALLOC, "cudaMallocHost: %s", cudaGetErrorString(e)));
     e = cudaMallocHost(&h->h_err, sizeof(uint32_t));
     if (e != cudaSuccess) return bail(fail(MPM_ERR_ALLOC, "cudaMallocHost: %s", cudaGetErrorString(e)));
@@ -463,13 +524,25 @@ mpm_status mpm_set_stream(mpm_handle *h, void *cuda_stream) {
     return MPM_OK;
 }
 
-mpm_status mpm_load_particles(mpm_handle *h, int64_t n, const float *x, const float *v, const float *F, const float *C,
-                              float particle_volume, int on_device) {
-    mpm_status st = check_handle(h);
-    if (st != MPM_OK) return st;
-    if (n < 0 || n > h->cfg.max_particles) return fail(MPM_ERR_ARG, "n = %lld outside [0, max_particles]", (long long)n);
-    if (n > 0 && !x) return fail(MPM_ERR_ARG, "x is required");
-    if (!(particle_volume > 0.f) || !std::isfinite(particle_volume)) return fail(MPM_ERR_ARG, "particle_volume must be > 0");
+}  // extern "C"
+
+namespace {
+
+// Replace the state of every environment: counts[e] particles of environment
+// e, stored env-major in x, v, F, C; volumes[e] its particle volume.
+mpm_status load_impl(mpm_handle *h, const int64_t *counts, const float *x, const float *v, const float *F,
+                     const float *C, const float *volumes, int on_device) {
+    int64_t total = 0;
+    for (int e = 0; e < h->n_envs; ++e) {
+        if (counts[e] < 0) return fail(MPM_ERR_ARG, "negative particle count for environment %d", e);
+        if (!(volumes[e] > 0.f) || !std::isfinite(volumes[e]))
+            return fail(MPM_ERR_ARG, "particle volume of environment %d must be > 0", e);
+        total += counts[e];
+    }
+    if (total > h->cfg.max_particles)
+        return fail(MPM_ERR_ARG, "%lld particles exceed max_particles", (long long)total);
+    if (total > 0 && !x) return fail(MPM_ERR_ARG, "x is required");
+    const int64_t n = total;
     const size_t N = (size_t)n;
     // inputs in device memory (staging copies for host inputs)
     const float *dx = x, *dv = v, *dF = F, *dC = C;
@@ -481,9 +554,13 @@ mpm_status mpm_load_particles(mpm_handle *h, int64_t n, const float *x, const fl
         if (F) { CK(cudaMemcpyAsync(sF, F, sizeof(float) * 9 * N, cudaMemcpyHostToDevice, h->stream)); dF = sF; }
         if (C) { CK(cudaMemcpyAsync(sC, C, sizeof(float) * 9 * N, cudaMemcpyHostToDevice, h->stream)); dC = sC; }
     }
-    h->particle_volume = particle_volume;
-    h->P.mass = h->cfg.rho * particle_volume;
-    h->P.stress_k = (float)((double)h->cfg.dt * particle_volume * 4.0 * (double)h->P.inv_dx * h->P.inv_dx);
+    h->particle_volume = volumes[0];
+    h->env_off[0] = 0;
+    for (int e = 0; e < h->n_envs; ++e) {
+        h->env_vol[e] = volumes[e];
+        h->env_off[e + 1] = h->env_off[e] + (uint32_t)counts[e];
+    }
+    h->envp_dirty = true;
     // graphs captured the old parameters
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.second);
     h->graphs.clear();
@@ -493,11 +570,15 @@ mpm_status mpm_load_particles(mpm_handle *h, int64_t n, const float *x, const fl
     c.step = k0;
     c.n_particles = (uint32_t)n;
     CK(cudaMemcpyAsync(h->fb.ctrl, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_env_off, h->env_off.data(), sizeof(uint32_t) * (h->n_envs + 1), cudaMemcpyHostToDevice,
+                       h->stream));
     CK(cudaStreamSynchronize(h->stream));   // the host Ctrl and input buffers must outlive the copies
+    mpm_status st = upload_env_params(h);
+    if (st != MPM_OK) return st;
     h->step = k0;
     h->n = n;
     h->taken = 0;
-    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n * h->n_envs;
     if (is_fused(h)) {
         for (int g = 0; g < 3; ++g) CK(cudaMemsetAsync(h->fb.G[g], 0, sizeof(float4) * nn, h->stream));
         CK(cudaMemsetAsync(h->sort.counts, 0, sizeof(uint32_t) * h->nblocks, h->stream));
@@ -516,11 +597,11 @@ mpm_status mpm_load_particles(mpm_handle *h, int64_t n, const float *x, const fl
     return enqueue_error_copy(h);
 }
 
-mpm_status mpm_set_tool_pose(mpm_handle *h, int32_t tool_id, const double pose[6], const float shape[8]) {
-    if (!h) return fail(MPM_ERR_ARG, "NULL handle");
+mpm_status set_tool_impl(mpm_handle *h, int32_t env, int32_t tool_id, const double pose[6], const float shape[8]) {
+    if (env < 0 || env >= h->n_envs) return fail(MPM_ERR_ARG, "environment %d out of range", env);
     if (tool_id < 0 || tool_id >= MPM_MAX_TOOLS) return fail(MPM_ERR_ARG, "tool_id %d out of range", tool_id);
     if (!pose || !shape) return fail(MPM_ERR_ARG, "NULL pose or shape");
-    HostTool &t = h->tools[tool_id];
+    HostTool &t = h->tools[(size_t)env * MPM_MAX_TOOLS + tool_id];
     const int kind = (int)shape[0];
     if (kind == MPM_TOOL_NONE) {
         t = HostTool();
@@ -541,6 +622,50 @@ mpm_status mpm_set_tool_pose(mpm_handle *h, int32_t tool_id, const double pose[6
     return MPM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+mpm_status mpm_load_particles(mpm_handle *h, int64_t n, const float *x, const float *v, const float *F, const float *C,
+                              float particle_volume, int on_device) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (h->n_envs != 1) return fail(MPM_ERR_STATE, "a handle with several environments loads with mpm_load_batch");
+    if (n < 0 || n > h->cfg.max_particles) return fail(MPM_ERR_ARG, "n = %lld outside [0, max_particles]", (long long)n);
+    return load_impl(h, &n, x, v, F, C, &particle_volume, on_device);
+}
+
+mpm_status mpm_load_batch(mpm_handle *h, const int64_t *counts, const float *x, const float *v, const float *F,
+                          const float *C, const float *particle_volumes, int on_device) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (!counts || !particle_volumes) return fail(MPM_ERR_ARG, "NULL counts or particle volumes");
+    return load_impl(h, counts, x, v, F, C, particle_volumes, on_device);
+}
+
+mpm_status mpm_set_env_material(mpm_handle *h, int32_t env, float E, float nu, float rho) {
+    if (!h) return fail(MPM_ERR_ARG, "NULL handle");
+    if (env < 0 || env >= h->n_envs) return fail(MPM_ERR_ARG, "environment %d out of range", env);
+    if (!(E >= 0.f) || !(nu >= 0.f) || !(nu < 0.5f) || !(rho > 0.f))
+        return fail(MPM_ERR_ARG, "need E >= 0, 0 <= nu < 0.5, rho > 0");
+    h->env_E[env] = E;
+    h->env_nu[env] = nu;
+    h->env_rho[env] = rho;
+    h->envp_dirty = true;   // applies from the next stress evaluation
+    return MPM_OK;
+}
+
+mpm_status mpm_set_env_tool_pose(mpm_handle *h, int32_t env, int32_t tool_id, const double pose[6],
+                                 const float shape[8]) {
+    if (!h) return fail(MPM_ERR_ARG, "NULL handle");
+    return set_tool_impl(h, env, tool_id, pose, shape);
+}
+
+mpm_status mpm_set_tool_pose(mpm_handle *h, int32_t tool_id, const double pose[6], const float shape[8]) {
+    if (!h) return fail(MPM_ERR_ARG, "NULL handle");
+    return set_tool_impl(h, 0, tool_id, pose, shape);
+}
+
 mpm_status mpm_step(mpm_handle *h, int32_t n_substeps) {
     mpm_status st = check_handle(h);
     if (st != MPM_OK) return st;
@@ -552,11 +677,11 @@ mpm_status mpm_step(mpm_handle *h, int32_t n_substeps) {
         for (auto &t : h->tools) std::memcpy(t.cur, t.tgt, sizeof t.cur);
         return MPM_OK;
     }
-    for (int first = 0; first < n_substeps; first += kMaxSubChunk) {
-        const int m = std::min(kMaxSubChunk, n_substeps - first);
+    for (int first = 0; first < n_substeps; first += h->sub_chunk) {
+        const int m = std::min(h->sub_chunk, n_substeps - first);
         if ((st = upload_frames(h, first, m, n_substeps)) != MPM_OK) return st;
         const bool last = first + m == n_substeps;
-        if ((st = run_chunk(h, m, last, h->P.ntools)) != MPM_OK) return st;
+        if ((st = run_chunk(h, m, last)) != MPM_OK) return st;
         if (is_fused(h)) h->step += (uint32_t)m;
     }
     h->taken += n_substeps;
@@ -619,7 +744,7 @@ mpm_status mpm_read_particles(mpm_handle *h, float *x, float *v, float *F, float
 
 static mpm_status ensure_dense(mpm_handle *h) {
     if (h->dense) return MPM_OK;
-    return dalloc_t(h, &h->dense, (size_t)h->P.n * h->P.n * h->P.n);
+    return dalloc_t(h, &h->dense, (size_t)h->P.n * h->P.n * h->P.n * h->n_envs);
 }
 
 // The grid the next sub-step starts from: fused pipelines keep it in
@@ -636,13 +761,13 @@ mpm_status mpm_read_grid(mpm_handle *h, float *grid, int on_device) {
     if (st != MPM_OK) return st;
     if (!grid) return fail(MPM_ERR_ARG, "NULL output");
     if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
-    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n * h->n_envs;
     const float4 *G = current_grid(h);
     if (on_device) {
-        launch_grid_to_dense(h->P.n, h->P.nb, G, (float4 *)grid, h->elem_grid, h->stream);
+        launch_grid_to_dense(h->P.n, h->P.nb, h->n_envs, G, (float4 *)grid, h->elem_grid, h->stream);
     } else {
         if ((st = ensure_dense(h)) != MPM_OK) return st;
-        launch_grid_to_dense(h->P.n, h->P.nb, G, h->dense, h->elem_grid, h->stream);
+        launch_grid_to_dense(h->P.n, h->P.nb, h->n_envs, G, h->dense, h->elem_grid, h->stream);
         CK(cudaMemcpyAsync(grid, h->dense, sizeof(float4) * nn, cudaMemcpyDeviceToHost, h->stream));
     }
     CK(cudaGetLastError());
@@ -654,7 +779,7 @@ mpm_status mpm_grid_velocity(mpm_handle *h, float *v, int on_device) {
     if (st != MPM_OK) return st;
     if (!v) return fail(MPM_ERR_ARG, "NULL output");
     if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
-    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n * h->n_envs;
     if ((st = upload_frames(h, 0, 1, 1)) != MPM_OK) return st;
     const float4 *G = current_grid(h);
     float *outp = v;
@@ -685,11 +810,12 @@ mpm_status mpm_read_order(mpm_handle *h, uint32_t *ids, uint32_t *keys) {
     if (h->n > 0) CK(cudaMemcpy(xi.data(), h->fb.P[par].xi, sizeof(float4) * h->n, cudaMemcpyDeviceToHost));
     size_t w = 0;
     for (uint32_t b = 0; b < h->nblocks; ++b) {
-        const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+        const uint32_t e0 = (b / h->nbe) * h->nbe, bl = b % h->nbe;
+        const int bx = bl % nb, by = (bl / nb) % nb, bz = bl / (nb * nb);
         for (int d = 26; d >= 0; --d) {
             const int sx = bx - (d % 3 - 1), sy = by - ((d / 3) % 3 - 1), sz = bz - (d / 9 - 1);
             if (sx < 0 || sy < 0 || sz < 0 || sx >= (int)nb || sy >= (int)nb || sz >= (int)nb) continue;
-            const BlockTab &t = tabs[block_id(sx, sy, sz, nb)];
+            const BlockTab &t = tabs[e0 + block_id(sx, sy, sz, nb)];
             if (t.stamp != h->step) continue;
             for (uint32_t p = 0; p < t.npass; ++p) {
                 if (t.first + p >= h->chunk_cap) return fail(MPM_ERR_STATE, "corrupt run table");

@@ -18,18 +18,30 @@ enum : uint32_t {
     kErrCfl = 8u,        // particle moved by more than one block in a sub-step
 };
 
-// Per-handle constants, passed by value to every kernel.
-struct DevParams {
-    int n;            // nodes per axis
-    int nb;           // 4x4x4 blocks per axis (n / 4)
-    int bound;        // sticky wall band
-    int ntools;       // number of tool slots in use (max active id + 1)
-    float dx, inv_dx, dt;
-    float gx, gy, gz;
+// Per-environment material, in a device table indexed by environment.
+struct EnvParams {
     float mass;       // m_p = rho V_p^0
     float mu, lam;    // Lame parameters (Eq. 6)
     float stress_k;   // dt V_p^0 4/dx^2 : A_p = m_p C_p - stress_k tau_p
+    int ntools;       // tool slots in use (highest active id + 1)
+    int pad[3];
+};
+
+// Per-handle constants, passed by value to every kernel.  A handle holds
+// n_envs independent environments on identical grids; grid block g of the
+// whole handle is block g % nbe of environment g / nbe.
+struct DevParams {
+    int n;            // nodes per axis
+    int nb;           // 4x4x4 blocks per axis (n / 4)
+    uint32_t nbe;     // blocks per environment (nb^3)
+    int n_envs;
+    int bound;        // sticky wall band
+    int tstride;      // tool frames per environment in a sub-step's frame table
+    float dx, inv_dx, dt;
+    float gx, gy, gz;
     float theta, fric;
+    const EnvParams *envp;     // n_envs entries
+    const uint32_t *env_off;   // n_envs + 1 particle-index offsets (environments are contiguous)
 };
 
 // One tool at one sub-step, in FP32 (computed on the host in FP64).
@@ -98,6 +110,21 @@ __host__ __device__ __forceinline__ uint32_t block_id(int bx, int by, int bz, in
 }
 __host__ __device__ __forceinline__ uint32_t node_addr(int i, int j, int k, int nb) {
     return block_id(i >> 2, j >> 2, k >> 2, nb) * 64u + (uint32_t)((i & 3) + 4 * ((j & 3) + 4 * (k & 3)));
+}
+// node (i,j,k) of environment e
+__host__ __device__ __forceinline__ uint32_t node_addr_env(uint32_t e, int i, int j, int k, int nb, uint32_t nbe) {
+    return e * nbe * 64u + node_addr(i, j, k, nb);
+}
+
+// Environment of global particle index p (environments occupy contiguous
+// index ranges env_off[e] .. env_off[e+1]).
+__device__ __forceinline__ uint32_t env_of_particle(uint32_t p, const DevParams &P) {
+    int lo = 0, hi = P.n_envs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.env_off[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    return (uint32_t)lo;
 }
 
 // ------------------------------------------------------------ arithmetic
@@ -187,16 +214,16 @@ __device__ __forceinline__ float tool_sdf(int kind, const float *dims, float px,
 // contact with the closest tool (z-buffer merge; Eqs. 11, 15-19 with the
 // friction clamped at zero tangential speed), then sticky walls.
 __device__ __forceinline__ float3 grid_node_update(float m, float mvx, float mvy, float mvz, int i, int j, int k,
-                                                   const DevParams &P, const ToolFrame *tools) {
+                                                   const DevParams &P, const ToolFrame *tools, int ntools) {
     if (!(m > 0.0f)) return make_float3(0.0f, 0.0f, 0.0f);
     float vx = mvx / m + P.dt * P.gx;
     float vy = mvy / m + P.dt * P.gy;
     float vz = mvz / m + P.dt * P.gz;
-    if (P.ntools > 0) {
+    if (ntools > 0) {
         const float xw = i * P.dx, yw = j * P.dx, zw = k * P.dx;
         float dmin = 3.0e38f, nbx = 0.f, nby = 0.f, nbz = 0.f;
         int id = -1;
-        for (int t = 0; t < P.ntools; ++t) {
+        for (int t = 0; t < ntools; ++t) {
             const ToolFrame &tf = tools[t];
             if (tf.kind < 0) continue;
             const float rx = xw - tf.T[0], ry = yw - tf.T[1], rz = zw - tf.T[2];

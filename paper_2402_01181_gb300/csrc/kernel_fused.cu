@@ -55,6 +55,8 @@ struct FusedSmem {
     // in place by the grid operation) and the block's inbox of incoming runs
     float4 graw[2][216];
     uint4 inbox[2][kInbox];
+    EnvParams ep[2];               // the block's environment: material
+    ToolFrame tools[2][kMaxTools]; // and its tool frames for this sub-step
     uint32_t items[2], bids[2];
     int acc[4][kArena];            // P2G arena over nodes [4b-1, 4b+6]^3 (fixed point, padded strides)
     // staged P2G inputs of one group: packed arena base, fx (3), q (3), A dx (9)
@@ -62,7 +64,6 @@ struct FusedSmem {
     float st_f[3][GROUP];
     float st_q[3][GROUP];
     float st_a[9][GROUP];
-    ToolFrame tools[kMaxTools];
     uint32_t cand_start[CMAX];     // first slot of each run
     uint32_t cand_pre[CMAX + 1];   // exclusive prefix of run lengths
     uint32_t lane_first[27], lane_off[27];
@@ -92,18 +93,32 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool va
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Start copying block b's grid region of G_k and its inbox into buffer buf.
+// Start copying global block b's grid region of G_k, its inbox, and its
+// environment's material and tool frames into buffer buf.
 __device__ __forceinline__ void prefetch_block(FusedSmem &s, int buf, uint32_t b, const uint4 *__restrict__ inbox_in,
-                                               const float4 *__restrict__ Gcur, int nb, int n, int tid) {
-    const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
-    for (int q = tid; q < 216 + kInbox; q += T) {
+                                               const float4 *__restrict__ Gcur, const DevParams &P,
+                                               const ToolFrame *__restrict__ tools, int tid) {
+    const uint32_t e = b / P.nbe, bl = b % P.nbe;
+    const int nb = P.nb, n = P.n;
+    const int bx = bl % nb, by = (bl / nb) % nb, bz = bl / (nb * nb);
+    constexpr int kTw = (int)(sizeof(ToolFrame) / 16);   // 16-byte words per frame
+    const int ntw = P.tstride * kTw;
+    for (int q = tid; q < 216 + kInbox + 2 + ntw; q += T) {
         if (q < 216) {
             const int i = 4 * bx + q % 6, j = 4 * by + (q / 6) % 6, k = 4 * bz + q / 36;
             const bool ok = i < n && j < n && k < n;
-            cp_async16(&s.graw[buf][q], ok ? (const void *)&Gcur[node_addr(i, j, k, nb)] : (const void *)Gcur, ok);
+            cp_async16(&s.graw[buf][q], ok ? (const void *)&Gcur[node_addr_env(e, i, j, k, nb, P.nbe)] : (const void *)Gcur,
+                       ok);
+        } else if (q < 216 + kInbox) {
+            const int x = q - 216;
+            cp_async16(&s.inbox[buf][x], &inbox_in[(size_t)b * kInbox + x], true);
+        } else if (q < 216 + kInbox + 2) {
+            const int x = q - 216 - kInbox;
+            cp_async16(reinterpret_cast<uint4 *>(&s.ep[buf]) + x, reinterpret_cast<const uint4 *>(&P.envp[e]) + x, true);
         } else {
-            const int e = q - 216;
-            cp_async16(&s.inbox[buf][e], &inbox_in[(size_t)b * kInbox + e], true);
+            const int x = q - 216 - kInbox - 2;
+            cp_async16(reinterpret_cast<uint4 *>(&s.tools[buf][0]) + x,
+                       reinterpret_cast<const uint4 *>(tools + (size_t)e * P.tstride) + x, true);
         }
     }
     cp_async_commit();
@@ -138,11 +153,8 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
     const uint32_t nparticles = ctrl->n_particles;
     const uint32_t nchunk_cap = B.nblocks + nparticles / T + 1;
     const int nb = P.nb, n = P.n;
-    const float m = P.mass;
+    const uint32_t nbe = P.nbe;
     uint32_t err = 0;
-
-    if (tid < P.ntools * (int)(sizeof(ToolFrame) / 4))
-        reinterpret_cast<float *>(s.tools)[tid] = reinterpret_cast<const float *>(tools)[tid];
 
     // 0. clear the grid blocks G_{k-1} touched, so that sub-step k+1 can scatter into it
     for (uint32_t q = blockIdx.x * T + tid; q < nclr * 64u; q += gridDim.x * T)
@@ -155,15 +167,19 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
         s.bids[0] = it < nact ? act[it] : 0u;
     }
     __syncthreads();
-    if (s.items[0] < nact) prefetch_block(s, 0, s.bids[0], inbox_in, Gcur, nb, n, tid);
+    if (s.items[0] < nact) prefetch_block(s, 0, s.bids[0], inbox_in, Gcur, P, tools, tid);
     cp_async_wait_all();
     __syncthreads();
 
     for (int cb = 0;; cb ^= 1) {
         const uint32_t item = s.items[cb];
         if (item >= nact) break;
-        const uint32_t b = s.bids[cb];
-        const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
+        const uint32_t b = s.bids[cb];                 // global block
+        const uint32_t env = b / nbe, bl = b % nbe;     // environment, block inside it
+        const uint32_t eb0 = env * nbe;                 // first global block of the environment
+        const int bx = bl % nb, by = (bl / nb) % nb, bz = bl / (nb * nb);
+        const EnvParams &ep = s.ep[cb];
+        const float m = ep.mass;
         // the next work item, fetched while this block is set up
         if (tid == T - 1) {
             const uint32_t it = atomicAdd(&ctrl->work, 1u);
@@ -178,7 +194,7 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
             const int i = 4 * bx + q % 6, j = 4 * by + (q / 6) % 6, k = 4 * bz + q / 36;
             const float4 g = gv[q];
             float3 v = make_float3(0.f, 0.f, 0.f);
-            if (i < n && j < n && k < n) v = grid_node_update(g.x, g.y, g.z, g.w, i, j, k, P, s.tools);
+            if (i < n && j < n && k < n) v = grid_node_update(g.x, g.y, g.z, g.w, i, j, k, P, s.tools[cb], ep.ntools);
             gv[q] = make_float4(v.x, v.y, v.z, 0.f);
         }
         for (int q = tid; q < 4 * kArena; q += T) (&s.acc[0][0])[q] = 0;
@@ -217,7 +233,7 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
                     const int d = 26 - lane;
                     const int sx = bx - dir_dx(d), sy = by - dir_dy(d), sz = bz - dir_dz(d);
                     if (sx >= 0 && sy >= 0 && sz >= 0 && sx < nb && sy < nb && sz < nb) {
-                        const BlockTab t = tin[block_id(sx, sy, sz, nb)];
+                        const BlockTab t = tin[eb0 + block_id(sx, sy, sz, nb)];
                         if (t.stamp == step) { np = t.npass; first = t.first; }
                     }
                 }
@@ -276,7 +292,7 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
         }
         __syncthreads();
         // start copying the next block's inputs; they land while this block computes
-        if (s.items[cb ^ 1] < nact) prefetch_block(s, cb ^ 1, s.bids[cb ^ 1], inbox_in, Gcur, nb, n, tid);
+        if (s.items[cb ^ 1] < nact) prefetch_block(s, cb ^ 1, s.bids[cb ^ 1], inbox_in, Gcur, P, tools, tid);
         const uint32_t ncand = s.ncand;
         const uint32_t total = s.total, npass = s.npass, out_base = s.out_base, chunk_first = s.chunk_first;
         const int ox = 4 * bx - 1, oy = 4 * by - 1, oz = 4 * bz - 1;   // arena origin
@@ -353,8 +369,8 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
                 }
                 // --- stress of the new state (Eqs. 5-6) and the P2G inputs (Eqs. 1-3)
                 float t[6];
-                kirchhoff(Fn, P.mu, P.lam, t, err);
-                const float kst = P.stress_k, dxs = P.dx;
+                kirchhoff(Fn, ep.mu, ep.lam, t, err);
+                const float kst = ep.stress_k, dxs = P.dx;
                 float A[9] = {(m * Cm[0] - kst * t[0]) * dxs, (m * Cm[1] - kst * t[1]) * dxs, (m * Cm[2] - kst * t[2]) * dxs,
                               (m * Cm[3] - kst * t[1]) * dxs, (m * Cm[4] - kst * t[3]) * dxs, (m * Cm[5] - kst * t[4]) * dxs,
                               (m * Cm[6] - kst * t[2]) * dxs, (m * Cm[7] - kst * t[4]) * dxs, (m * Cm[8] - kst * t[5]) * dxs};
@@ -396,13 +412,13 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
                             const float rz = qz + A[7] * jj + A[8] * kk;
                             for (int ii = 0; ii < 3; ++ii) {
                                 const float w = wx2[ii] * wjk;
-                                atomicAdd(&Gnext[node_addr(hx + ii, hy + jj, hz + kk, nb)],
+                                atomicAdd(&Gnext[node_addr_env(env, hx + ii, hy + jj, hz + kk, nb, nbe)],
                                           make_float4(w * m, w * (rx + A[0] * ii), w * (ry + A[3] * ii), w * (rz + A[6] * ii)));
                             }
                         }
                     for (int c = 0; c < 8; ++c) {
                         const int gi = (hx + 2 * (c & 1)) >> 2, gj = (hy + (c & 2)) >> 2, gk = (hz + ((c >> 1) & 2)) >> 2;
-                        mark_clear(B, block_id(gi, gj, gk, nb), step + 1, m3n);
+                        mark_clear(B, eb0 + block_id(gi, gj, gk, nb), step + 1, m3n);
                     }
                 }
                 // --- destination block of the new state
@@ -441,7 +457,7 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
                     cout[chunk_first + pass].run[lane] = make_uint2(pbase + incl - run, run);
                     const int tx = bx + dir_dx(lane), ty = by + dir_dy(lane), tz = bz + dir_dz(lane);
                     if (run > 0u && tx >= 0 && ty >= 0 && tz >= 0 && tx < nb && ty < nb && tz < nb) {
-                        uint4 *dst = inbox_out + (size_t)block_id(tx, ty, tz, nb) * kInbox;
+                        uint4 *dst = inbox_out + (size_t)(eb0 + block_id(tx, ty, tz, nb)) * kInbox;
                         if (pass < (uint32_t)kNpMax)
                             dst[lane * kNpMax + pass] = make_uint4(pbase + incl - run, run, step + 1, 0u);
                         else
@@ -511,7 +527,7 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
                     if (am != 0 || px != 0 || py != 0 || pz != 0) {
                         const int i = ox + lx8, jn = oy + ly8, k = oz + lz8;
                         if (i >= 0 && jn >= 0 && k >= 0 && i < n && jn < n && k < n)
-                            atomicAdd(&Gnext[node_addr(i, jn, k, nb)],
+                            atomicAdd(&Gnext[node_addr_env(env, i, jn, k, nb, nbe)],
                                       make_float4((float)am * um, (float)px * up, (float)py * up, (float)pz * up));
                         s.acc[0][a] = 0; s.acc[1][a] = 0; s.acc[2][a] = 0; s.acc[3][a] = 0;
                     }
@@ -528,7 +544,7 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
         if (warp == 0 && lane < 27) {
             const int tx = bx + dir_dx(lane), ty = by + dir_dy(lane), tz = bz + dir_dz(lane);
             if (tx >= 0 && ty >= 0 && tz >= 0 && tx < nb && ty < nb && tz < nb) {
-                const uint32_t tb = block_id(tx, ty, tz, nb);
+                const uint32_t tb = eb0 + block_id(tx, ty, tz, nb);
                 if ((s.mask >> lane) & 1u) {
                     if (atomicExch(&B.astamp[tb], step + 1) != step + 1)
                         act_next[atomicAdd(&ctrl->nactive[par ^ 1], 1u)] = tb;

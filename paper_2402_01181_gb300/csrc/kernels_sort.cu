@@ -9,12 +9,16 @@
 
 namespace gbmpm {
 
-__device__ __forceinline__ uint32_t particle_block_key(float x, float y, float z, const DevParams &P, uint32_t &err) {
+// Global block key of particle p: environment * blocks-per-environment + the
+// block of its stencil base inside the environment's grid.
+__device__ __forceinline__ uint32_t particle_block_key(uint32_t p, float x, float y, float z, const DevParams &P,
+                                                       uint32_t &err) {
     int bx, by, bz;
     stencil_axis(x, P.inv_dx, P.n, bx, err);
     stencil_axis(y, P.inv_dx, P.n, by, err);
     stencil_axis(z, P.inv_dx, P.n, bz, err);
-    return block_id(bx >> 2, by >> 2, bz >> 2, P.nb);
+    const uint32_t e = P.n_envs > 1 ? env_of_particle(p, P) : 0u;
+    return e * P.nbe + block_id(bx >> 2, by >> 2, bz >> 2, P.nb);
 }
 
 __global__ void k_keys_hist(DevParams P, const float *__restrict__ x, uint32_t n, uint32_t *__restrict__ keys,
@@ -28,7 +32,8 @@ __global__ void k_keys_hist(DevParams P, const float *__restrict__ x, uint32_t n
         if (ok) {
             const float px = x[3 * (size_t)p], py = x[3 * (size_t)p + 1], pz = x[3 * (size_t)p + 2];
             if (!finite3(px, py, pz)) err |= kErrNumeric;
-            key = particle_block_key(isfinite(px) ? px : 0.f, isfinite(py) ? py : 0.f, isfinite(pz) ? pz : 0.f, P, err);
+            key = particle_block_key(p, isfinite(px) ? px : 0.f, isfinite(py) ? py : 0.f, isfinite(pz) ? pz : 0.f, P,
+                                     err);
             keys[p] = key;
         }
         // one atomic per distinct key in the warp
@@ -145,7 +150,7 @@ __global__ void __launch_bounds__(256) k_segment_sort(const uint32_t *__restrict
 
 void launch_block_sort(const DevParams &P, const float *x, uint32_t n, const SortScratch &s, Ctrl *ctrl, int grid,
                        cudaStream_t st) {
-    const uint32_t m = (uint32_t)P.nb * P.nb * P.nb;
+    const uint32_t m = P.nbe * (uint32_t)P.n_envs;
     if (n > 0) k_keys_hist<<<grid, 256, 0, st>>>(P, x, n, s.keys, s.counts, ctrl);
     k_scan_counts<<<1, 1024, 0, st>>>(s.counts, m, s.offsets, s.cursor);
     if (n == 0) return;
@@ -200,11 +205,12 @@ __global__ void k_init_tables(DevParams P, const uint32_t *__restrict__ offsets,
         B.inbox[par][(size_t)b * kInbox + 13 * kNpMax] = make_uint4(off, c, step, 0u);
         B.astamp[b] = step;
         B.alist[par][atomicAdd(&B.ctrl->nactive[par], 1u)] = b;
-        const int bx = b % P.nb, by = (b / P.nb) % P.nb, bz = b / (P.nb * P.nb);
+        const uint32_t e = b / P.nbe, bl = b % P.nbe;
+        const int bx = bl % P.nb, by = (bl / P.nb) % P.nb, bz = bl / (P.nb * P.nb);
         for (int d = 0; d < 27; ++d) {
             const int sx = bx + d % 3 - 1, sy = by + (d / 3) % 3 - 1, sz = bz + d / 9 - 1;
             if (sx < 0 || sy < 0 || sz < 0 || sx >= P.nb || sy >= P.nb || sz >= P.nb) continue;
-            const uint32_t g = block_id(sx, sy, sz, P.nb);
+            const uint32_t g = e * P.nbe + block_id(sx, sy, sz, P.nb);
             if (atomicExch(&B.gstamp[g], step) != step) B.clist[m3][atomicAdd(&B.ctrl->nclear[m3], 1u)] = g;
         }
     }

@@ -20,10 +20,12 @@ __global__ void __launch_bounds__(256) k_p2g_scatter(DevParams P, PState S, VCSt
         const float F[9] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, S.f2[s]};
         const float4 c0 = V.vc0[s], c1 = V.vc1[s], c2 = V.vc2[s];
         const float C[9] = {c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
+        const uint32_t e = P.n_envs > 1 ? env_of_particle(__float_as_uint(xi.w), P) : 0u;
+        const EnvParams ep = P.envp[e];
         float t[6];
-        kirchhoff(F, P.mu, P.lam, t, err);
+        kirchhoff(F, ep.mu, ep.lam, t, err);
         if (!finite3(xi.x, xi.y, xi.z) || !finite3(c0.x, c0.y, c0.z)) err |= kErrNumeric;
-        const float m = P.mass, k = P.stress_k;
+        const float m = ep.mass, k = ep.stress_k;
         // A scaled by dx (so that A (x_i - x_p) = A' (o - fx))
         const float A[9] = {(m * C[0] - k * t[0]) * P.dx, (m * C[1] - k * t[1]) * P.dx, (m * C[2] - k * t[2]) * P.dx,
                             (m * C[3] - k * t[1]) * P.dx, (m * C[4] - k * t[3]) * P.dx, (m * C[5] - k * t[4]) * P.dx,
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(256) k_p2g_scatter(DevParams P, PState S, VCSt
                 for (int ii = 0; ii < 3; ++ii) {
                     const float w = wx[ii] * wjk;
                     const float4 val = make_float4(w * m, w * (rx + A[0] * ii), w * (ry + A[3] * ii), w * (rz + A[6] * ii));
-                    atomicAdd(&G[node_addr(bx + ii, by + jj, bz + kk, P.nb)], val);
+                    atomicAdd(&G[node_addr_env(e, bx + ii, by + jj, bz + kk, P.nb, P.nbe)], val);
                 }
             }
         }
@@ -65,7 +67,8 @@ __global__ void __launch_bounds__(256) k_p2g_scatter(DevParams P, PState S, VCSt
 __global__ void __launch_bounds__(256) k_grid_update_dense(DevParams P, float4 *__restrict__ G,
                                                             const ToolFrame *__restrict__ tools) {
     __shared__ ToolFrame s_tools[kMaxTools];
-    if (threadIdx.x < P.ntools * (sizeof(ToolFrame) / 4))
+    const int ntools = P.envp[0].ntools;
+    if (threadIdx.x < ntools * (sizeof(ToolFrame) / 4))
         reinterpret_cast<float *>(s_tools)[threadIdx.x] = reinterpret_cast<const float *>(tools)[threadIdx.x];
     __syncthreads();
     const uint32_t total = (uint32_t)P.n * P.n * P.n;
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(256) k_grid_update_dense(DevParams P, float4 *
         const uint32_t b = g >> 6, l = g & 63u;
         const int bx = b % P.nb, by = (b / P.nb) % P.nb, bz = b / (P.nb * P.nb);
         const int i = bx * 4 + (l & 3), j = by * 4 + ((l >> 2) & 3), k = bz * 4 + (l >> 4);
-        const float3 v = grid_node_update(node.x, node.y, node.z, node.w, i, j, k, P, s_tools);
+        const float3 v = grid_node_update(node.x, node.y, node.z, node.w, i, j, k, P, s_tools, ntools);
         G[g] = make_float4(node.x, v.x, v.y, v.z);
     }
 }
@@ -196,28 +199,29 @@ __global__ void k_read_out(PState S, VCState V, uint32_t n, float *__restrict__ 
 }
 
 // Blocked grid -> dense [i][j][k] (k fastest) float4 rows.
-__global__ void k_grid_to_dense(int n, int nb, const float4 *__restrict__ G, float4 *__restrict__ out) {
-    const uint32_t total = (uint32_t)n * n * n;
+__global__ void k_grid_to_dense(int n, int nb, int n_envs, const float4 *__restrict__ G, float4 *__restrict__ out) {
+    const uint32_t per = (uint32_t)n * n * n, total = per * (uint32_t)n_envs;
+    const uint32_t nbe = (uint32_t)nb * nb * nb;
     for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < total; d += gridDim.x * blockDim.x) {
-        const int k = d % n, j = (d / n) % n, i = d / (n * n);
-        out[d] = G[node_addr(i, j, k, nb)];
+        const uint32_t e = d / per, r = d % per;
+        const int k = r % n, j = (r / n) % n, i = r / (n * n);
+        out[d] = G[node_addr_env(e, i, j, k, nb, nbe)];
     }
 }
 
-// Grid operation of every node of the blocked grid G (m, mv) into dense
-// [i][j][k] velocity rows (3 floats).
+// Grid operation of every node of the blocked grids G (m, mv) of all
+// environments into dense [e][i][j][k] velocity rows (3 floats); tools is the
+// frame table of one sub-step (tstride frames per environment).
 __global__ void k_grid_velocity_dense(DevParams P, const float4 *__restrict__ G, const ToolFrame *__restrict__ tools,
                                       float *__restrict__ out) {
-    __shared__ ToolFrame s_tools[kMaxTools];
-    if (threadIdx.x < P.ntools * (sizeof(ToolFrame) / 4))
-        reinterpret_cast<float *>(s_tools)[threadIdx.x] = reinterpret_cast<const float *>(tools)[threadIdx.x];
-    __syncthreads();
     const int n = P.n;
-    const uint32_t total = (uint32_t)n * n * n;
+    const uint32_t per = (uint32_t)n * n * n, total = per * (uint32_t)P.n_envs;
     for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < total; d += gridDim.x * blockDim.x) {
-        const int k = d % n, j = (d / n) % n, i = d / (n * n);
-        const float4 g = G[node_addr(i, j, k, P.nb)];
-        const float3 v = grid_node_update(g.x, g.y, g.z, g.w, i, j, k, P, s_tools);
+        const uint32_t e = d / per, r = d % per;
+        const int k = r % n, j = (r / n) % n, i = r / (n * n);
+        const float4 g = G[node_addr_env(e, i, j, k, P.nb, P.nbe)];
+        const float3 v = grid_node_update(g.x, g.y, g.z, g.w, i, j, k, P, tools + (size_t)e * P.tstride,
+                                          P.envp[e].ntools);
         out[3 * (size_t)d] = v.x;
         out[3 * (size_t)d + 1] = v.y;
         out[3 * (size_t)d + 2] = v.z;
@@ -249,8 +253,8 @@ void launch_read_out(const PState &S, const VCState &V, uint32_t n, float *x, fl
     if (n == 0) return;
     k_read_out<<<grid, 256, 0, st>>>(S, V, n, x, v, F, C);
 }
-void launch_grid_to_dense(int n, int nb, const float4 *G, float4 *out, int grid, cudaStream_t st) {
-    k_grid_to_dense<<<grid, 256, 0, st>>>(n, nb, G, out);
+void launch_grid_to_dense(int n, int nb, int n_envs, const float4 *G, float4 *out, int grid, cudaStream_t st) {
+    k_grid_to_dense<<<grid, 256, 0, st>>>(n, nb, n_envs, G, out);
 }
 void launch_grid_velocity_dense(const DevParams &P, const float4 *G, const ToolFrame *tools, float *out, int grid,
                                 cudaStream_t st) {

@@ -21,7 +21,7 @@ void launch_load_identity(const float *x, const float *v, const float *F, const 
                           const VCState &V, Ctrl *ctrl, int grid, cudaStream_t st);
 void launch_read_out(const PState &S, const VCState &V, uint32_t n, float *x, float *v, float *F, float *C, int grid,
                      cudaStream_t st);
-void launch_grid_to_dense(int n, int nb, const float4 *G, float4 *out, int grid, cudaStream_t st);
+void launch_grid_to_dense(int n, int nb, int n_envs, const float4 *G, float4 *out, int grid, cudaStream_t st);
 void launch_grid_velocity_dense(const DevParams &P, const float4 *G, const ToolFrame *tools, float *out, int grid,
                                 cudaStream_t st);
 

@@ -77,10 +77,11 @@ extern "C" mpm_status mpm_block_sort_noalloc(const float *x, int64_t n, int32_t 
     if (st != MPM_OK) return st;
     const cudaStream_t stream = (cudaStream_t)cuda_stream;
     const uint32_t nb = (uint32_t)n_grid / 4u, m = nb * nb * nb;
-
     DevParams P{};
     P.n = n_grid;
     P.nb = (int)nb;
+    P.nbe = m;
+    P.n_envs = 1;
     P.dx = 1.0f / (float)n_grid;
     P.inv_dx = (float)n_grid;
     Ctrl *ctrl = reinterpret_cast<Ctrl *>(base);

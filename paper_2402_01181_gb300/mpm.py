@@ -43,7 +43,7 @@ class mpm_config(ct.Structure):
     _fields_ = [("n_grid", ct.c_int32), ("bound", ct.c_int32), ("dt", ct.c_float),
                 ("gravity", ct.c_float * 3), ("E", ct.c_float), ("nu", ct.c_float), ("rho", ct.c_float),
                 ("theta", ct.c_float), ("friction_mu", ct.c_float), ("pipeline", ct.c_int32),
-                ("max_particles", ct.c_int64)]
+                ("n_envs", ct.c_int32), ("max_particles", ct.c_int64)]
 
 
 mpm_alloc_fn = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
@@ -61,6 +61,10 @@ SIGNATURES = [
     ("mpm_load_particles", ct.c_int, [ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                       ct.c_float, ct.c_int]),
     ("mpm_set_tool_pose", ct.c_int, [ct.c_void_p, ct.c_int32, _DP, _FP]),
+    ("mpm_load_batch", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                  ct.c_void_p, _FP, ct.c_int]),
+    ("mpm_set_env_material", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_float, ct.c_float, ct.c_float]),
+    ("mpm_set_env_tool_pose", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_int32, _DP, _FP]),
     ("mpm_step", ct.c_int, [ct.c_void_p, ct.c_int32]),
     ("mpm_read_particles", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int]),
     ("mpm_last_error", ct.c_char_p, []),
@@ -96,6 +100,9 @@ mpm_create = lib.mpm_create
 mpm_destroy = lib.mpm_destroy
 mpm_load_particles = lib.mpm_load_particles
 mpm_set_tool_pose = lib.mpm_set_tool_pose
+mpm_load_batch = lib.mpm_load_batch
+mpm_set_env_material = lib.mpm_set_env_material
+mpm_set_env_tool_pose = lib.mpm_set_env_tool_pose
 mpm_step = lib.mpm_step
 mpm_read_particles = lib.mpm_read_particles
 mpm_num_particles = lib.mpm_num_particles
@@ -126,7 +133,7 @@ def check(status: int) -> int:
 
 
 def make_config(n_grid, dt, E, nu, rho, gravity=(0.0, -9.8, 0.0), bound=3, theta=0.0, friction=0.0,
-                pipeline=MPM_PIPELINE_FUSED, max_particles=1) -> mpm_config:
+                pipeline=MPM_PIPELINE_FUSED, max_particles=1, n_envs=1) -> mpm_config:
     c = mpm_config()
     c.n_grid = int(n_grid)
     c.bound = int(bound)
@@ -136,6 +143,7 @@ def make_config(n_grid, dt, E, nu, rho, gravity=(0.0, -9.8, 0.0), bound=3, theta
     c.E, c.nu, c.rho = float(E), float(nu), float(rho)
     c.theta, c.friction_mu = float(theta), float(friction)
     c.pipeline = int(pipeline)
+    c.n_envs = int(n_envs)
     c.max_particles = int(max_particles)
     return c
 
@@ -207,6 +215,27 @@ class Sim:
             check(mpm_load_particles(self.h, n, *ptrs, ct.c_float(particle_volume), 0))
         self.n = n
 
+    def load_batch(self, xs, volumes, vs=None, Fs=None, Cs=None):
+        """Host arrays per environment (lists); every output concatenates the
+        environments in this order."""
+        counts = (ct.c_int64 * len(xs))(*[int(np.asarray(x).shape[0]) for x in xs])
+        vol = np.ascontiguousarray(np.asarray(volumes, dtype=np.float32))
+        cat = lambda arrs, c: None if arrs is None else np.ascontiguousarray(
+            np.concatenate([np.asarray(a, np.float32).reshape(-1, c) for a in arrs]))
+        arrs = [cat(xs, 3), cat(vs, 3), cat(Fs, 9), cat(Cs, 9)]
+        ptrs = [None if a is None else a.ctypes.data_as(ct.c_void_p) for a in arrs]
+        check(mpm_load_batch(self.h, counts, *ptrs, vol.ctypes.data_as(_FP), 0))
+        self.n = int(sum(counts))
+        self.counts = [int(c) for c in counts]
+
+    def set_env_material(self, env, E, nu, rho):
+        check(mpm_set_env_material(self.h, int(env), float(E), float(nu), float(rho)))
+
+    def set_env_tool(self, env, tool_id, pose, shape):
+        p = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(6))
+        s = np.ascontiguousarray(np.asarray(shape, dtype=np.float32).reshape(8))
+        check(mpm_set_env_tool_pose(self.h, int(env), int(tool_id), p.ctypes.data_as(_DP), s.ctypes.data_as(_FP)))
+
     def set_tool(self, tool_id, pose, shape):
         p = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(6))
         s = np.ascontiguousarray(np.asarray(shape, dtype=np.float32).reshape(8))
@@ -233,16 +262,16 @@ class Sim:
         check(mpm_read_particles(self.h, *ptrs, 1))
 
     def read_grid(self):
-        n = self.cfg.n_grid
-        g = np.empty((n, n, n, 4), np.float32)
+        n, ne = self.cfg.n_grid, max(1, self.cfg.n_envs)
+        g = np.empty((ne, n, n, n, 4), np.float32)
         check(mpm_read_grid(self.h, g.ctypes.data_as(ct.c_void_p), 0))
-        return g
+        return g[0] if ne == 1 else g
 
     def grid_velocity(self):
-        n = self.cfg.n_grid
-        g = np.empty((n, n, n, 3), np.float32)
+        n, ne = self.cfg.n_grid, max(1, self.cfg.n_envs)
+        g = np.empty((ne, n, n, n, 3), np.float32)
         check(mpm_grid_velocity(self.h, g.ctypes.data_as(ct.c_void_p), 0))
-        return g
+        return g[0] if ne == 1 else g
 
     def read_order(self):
         ids = np.empty(self.n, np.uint32)

@@ -219,3 +219,34 @@ def random_state(x: np.ndarray, seed: int, v_scale=0.5, c_scale=2.0, f_dev=0.15)
     C = (c_scale * (2 * rng.random((n, 9)) - 1)).astype(np.float32)
     F = (np.eye(3).reshape(1, 9) + f_dev * (2 * rng.random((n, 9)) - 1)).astype(np.float32)
     return v, C, F
+
+
+def batch_envs(n_envs: int = 256, seed: int = 0, n_min: int = 5000, n_max: int = 40000) -> List[Scene]:
+    """Independent tissue scenes for batched stepping, each on its own 64^3
+    grid: N_e uniform in [n_min, n_max], a slab 0.6 s x 0.1 x 0.6 s m with
+    s = sqrt(N_e / 30000) (so the particle density matches slab30k),
+    E_e in [2e3, 2e4] Pa, nu_e in [0.2, 0.45], and a capsule following the
+    slab30k trajectory shifted by an x,z offset in [-0.1, 0.1] m and pressing
+    to a depth in [0.02, 0.05] m."""
+    rng = np.random.default_rng(seed)
+    n = 64
+    dx = 1.0 / n
+    y0 = 3 * dx
+    out = []
+    for e in range(n_envs):
+        N = int(rng.integers(n_min, n_max + 1))
+        sz = 0.6 * np.sqrt(N / 30000.0)
+        x = uniform_box((0.5 - sz / 2, y0, 0.5 - sz / 2), (0.5 + sz / 2, y0 + 0.1, 0.5 + sz / 2), N,
+                        int(rng.integers(1 << 31)))
+        E = float(rng.uniform(2e3, 2e4))
+        nu = float(rng.uniform(0.2, 0.45))
+        off = rng.uniform(-0.1, 0.1, size=2)
+        depth = float(rng.uniform(0.02, 0.05))
+        r, h = 0.02, 0.15
+        tip0 = y0 + 0.1 + 0.005
+        p0 = np.array([0.5 + off[0], tip0 + r + h, 0.5 + off[1], 0.0, 0.0, 0.0])
+        pose = _linear_path(p0, [(1000, (0.0, -depth, 0.0)), (2000, (0.10, -depth, 0.0))])
+        out.append(Scene("env%d" % e, n_grid=n, dt=5e-5, E=E, nu=nu, rho=1e3, x=x,
+                         particle_volume=sz * 0.1 * sz / N, friction=0.3,
+                         tools=[Tool(capsule_shape(r, h), pose)]))
+    return out

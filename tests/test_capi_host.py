@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_config_struct_matches_header(lib):
     # offsets follow the C layout of mpm_config (int64 at the end is 8-aligned)
     c = lib.mpm_config
-    assert c.max_particles.offset == 48 and ct.sizeof(c) == 56
+    assert c.n_envs.offset == 48 and c.max_particles.offset == 56 and ct.sizeof(c) == 64
 
 
 def test_argument_validation_without_gpu(lib):
