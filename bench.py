@@ -1,7 +1,7 @@
 """Benchmark of the GB300 MLS-MPM step.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                [--workload block1m|slab30k|block8m|cube8k] [--substeps S]
+                [--workload block1m|slab30k|slab30k_sdf|block8m|cube8k] [--substeps S]
                 [--pipeline fused|split]
 
 A benchmark step is one call of mpm_step with S sub-steps (default 25, one
@@ -153,7 +153,7 @@ def run_gpu_workload(name, args, rank, device, barrier, max_over_ranks, with_e2e
     def frame():
         s = s_next[0]
         for t, tool in tool_frames:
-            sim.set_tool(t, tool.pose(s + S - 1), tool.shape)
+            sim.set_tool(t, tool.pose(s + S - 1), tool.shape, tool.field)
         sim.step(S)
         s_next[0] = s + S
 
@@ -385,6 +385,12 @@ def main():
                   "value": r2["n"] * S * r2["steps"] * world / (r2["t_ms"] / 1e3),
                   "ms_per_step": r2["t_ms"] / r2["steps"],
                   "e2e": r2["n"] * S * r2["steps"] * world / (r2["t_e2e_ms"] / 1e3)}
+        # the same slab with the tool as a sampled 256^3 distance field
+        r3 = run_gpu_workload("slab30k_sdf", args, rank, device, barrier, max_over_ranks, with_e2e=False,
+                              steps=max(args.steps, 20))
+        second["sampled_field"] = {"workload": "slab30k_sdf", "field_res": 256,
+                                   "value": r3["n"] * S * r3["steps"] * world / (r3["t_ms"] / 1e3),
+                                   "ms_per_step": r3["t_ms"] / r3["steps"]}
 
     batched = None
     if not args.no_batched:

@@ -56,12 +56,14 @@ typedef enum mpm_status {
 
 enum {
     MPM_MAX_TOOLS = 8,
+    MPM_MAX_FIELDS = 16,      /* sampled distance fields per handle */
+    MPM_MAX_FIELD_RES = 1024, /* samples per axis of one field */
     MPM_PIPELINE_FUSED = 0, /* block-sorted particles; one fused kernel per sub-step */
     MPM_PIPELINE_SPLIT = 1  /* unsorted particles; P2G, grid and G2P as separate kernels */
 };
 
 /* Tool shape kinds, shape[0] of mpm_set_tool_pose. */
-enum { MPM_TOOL_NONE = -1, MPM_TOOL_CAPSULE = 0, MPM_TOOL_BOX = 1 };
+enum { MPM_TOOL_NONE = -1, MPM_TOOL_CAPSULE = 0, MPM_TOOL_BOX = 1, MPM_TOOL_SAMPLED = 2 };
 
 typedef struct mpm_config {
     int32_t n_grid;         /* nodes per axis: a power of two in [8, 512]; dx = 1/n_grid */
@@ -135,7 +137,8 @@ mpm_status mpm_set_env_tool_pose(mpm_handle *h, int32_t env, int32_t tool_id, co
  * point p sits at R p + T, R = exp([r]_x); grid nodes are mapped to the tool
  * frame by Eq. 11.  shape: 8 floats, shape[0] = kind; capsule: shape[1] =
  * radius, shape[2] = half-length of the axis segment along local y; box:
- * shape[1..3] = half extents; kind MPM_TOOL_NONE removes the tool.  The pose
+ * shape[1..3] = half extents; sampled: shape[1] = a field id returned by
+ * mpm_add_sampled_field; kind MPM_TOOL_NONE removes the tool.  The pose
  * is the target for the end of the next mpm_step call: during that call the
  * tool moves uniformly (constant linear and angular velocity) from its
  * current pose to the target, and that rigid velocity is v_co of Eq. 15.
@@ -144,6 +147,26 @@ mpm_status mpm_set_env_tool_pose(mpm_handle *h, int32_t env, int32_t tool_id, co
  * Host arrays. */
 mpm_status mpm_set_tool_pose(mpm_handle *h, int32_t tool_id, const double pose[6],
                              const float shape[8]);
+
+/* Register a distance field precomputed in a tool's reference frame (the
+ * offline SDF of Sec. III-C, Eqs. 12-14) for tools of kind MPM_TOOL_SAMPLED.
+ * samples: res^3 floats, x fastest: samples[(k*res + j)*res + i] is the
+ * signed distance at origin + spacing*(i, j, k) (reference frame, metres;
+ * negative inside the tool).  The paper's field is res = 256 with
+ * spacing = 1/256 and origin 0.  At a grid node with reference-frame position
+ * x_ref the distance is the sample at floor((x_ref - origin)/spacing) on each
+ * axis (Eq. 12) and the contact normal is the central difference of the
+ * neighbouring samples (Eq. 14; one-sided at the faces of the field),
+ * normalised; nodes outside the sampled volume are not in contact with the
+ * tool.  res in [1, MPM_MAX_FIELD_RES]; at most MPM_MAX_FIELDS fields per
+ * handle (MPM_ERR_CAPACITY beyond).  The samples are copied into device
+ * memory owned by the handle (freed by mpm_destroy), so the caller's array
+ * may be released on return; on_device != 0: samples is a device pointer,
+ * otherwise a host array (checked for NaN).  Synchronises the stream.  Every
+ * environment of the handle may use the field; *field_id receives its id
+ * (0, 1, ... in registration order). */
+mpm_status mpm_add_sampled_field(mpm_handle *h, int32_t res, const double origin[3], double spacing,
+                                 const float *samples, int on_device, int32_t *field_id);
 
 /* Advance n_substeps >= 0 sub-steps (P2G, grid operation, G2P; Sec. III-B).
  * Asynchronous on the handle's stream.  The fused pipeline folds a stable

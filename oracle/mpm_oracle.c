@@ -27,8 +27,11 @@
  *   - Grid velocity is formed only where m_i > 0; gravity is added after
  *     Eq. 7; sticky walls zero every component at nodes within `bound` nodes
  *     of the domain faces, applied after tool handling.
- *   - Tools use analytic distance functions (capsule, box) and their analytic,
- *     normalised gradients in place of the sampled SDF of Eqs. 12-14; the
+ *   - Tools use analytic distance functions (capsule, box) with their
+ *     analytic, normalised gradients, or a sampled distance field (Eqs. 12-14)
+ *     read at the sample floor((x_ref - o) / h) with the central-difference
+ *     normal of Eq. 14 (one-sided at the faces of the volume), normalised;
+ *     points outside the sampled volume are not in contact; the
  *     friction update of Eq. 18 is clamped at zero tangential speed; nodes
  *     with v_n >= 0 are left unchanged; several tools are merged by minimum
  *     distance with the lowest tool index winning ties (the z-buffer of
@@ -54,13 +57,17 @@ typedef struct {
 /* One rigid tool at one sub-step: world position of a reference-frame point
  * is x = R x_ref + T (Eq. 11 inverts this). */
 typedef struct {
-    int32_t kind;         /* 0 capsule: dims = (radius, half-length along local y); 1 box: half extents */
-    int32_t pad;
+    int32_t kind;         /* 0 capsule: dims = (radius, half-length along local y); 1 box: half extents;
+                             2 sampled distance field: dims = reference-frame position of sample (0,0,0) */
+    int32_t res;          /* kind 2: samples per axis */
     double dims[3];
     double R[9];          /* row-major rotation */
     double T[3];
     double u[3];          /* linear velocity of the reference point T */
     double w[3];          /* angular velocity */
+    double h;             /* kind 2: sample spacing (the dx of Eq. 13) */
+    const float *sdf;     /* kind 2: res^3 samples, sample (i,j,k) at sdf[(k res + j) res + i]
+                             holds the distance at dims + h (i, j, k) */
 } orc_tool;
 
 typedef struct {
@@ -292,7 +299,9 @@ void orc_tool_frames(int32_t kind, const double *dims, const double *pose0,
         const double s = (double)(k + 1) / (double)nsub;
         orc_tool *t = out + k;
         t->kind = kind;
-        t->pad = 0;
+        t->res = 0;
+        t->h = 0.0;
+        t->sdf = NULL;
         for (int d = 0; d < 3; ++d) t->dims[d] = dims[d];
         double rs[3] = {s * phi[0], s * phi[1], s * phi[2]}, Rs[9];
         orc_rotvec_to_matrix(rs, Rs);
@@ -339,13 +348,56 @@ double orc_sdf(int32_t kind, const double *dims, const double *p, double *nrm)
     return q[a];
 }
 
+/* Sampled distance field, Eqs. 12-14.  Eq. 12 indexes the precomputed field
+ * by x_ref / dx; with the field's first sample at o the index of a
+ * reference-frame point is floor((p - o) / h) on each axis.  The distance is
+ * that sample; the normal is Eq. 14's central difference of the neighbouring
+ * samples (a one-sided difference where the neighbour would lie outside the
+ * field), normalised.  Returns +inf outside the field.  cell_margin (optional):
+ * distance of p from the nearest cell face, the floor decision's margin. */
+double orc_sdf_sampled(const float *sdf, int32_t res, const double *o, double h,
+                       const double *p, double *nrm, double *cell_margin)
+{
+    int64_t c[3];
+    double cm = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        const double u = (p[a] - o[a]) / h;
+        const double f = floor(u);
+        const double gap = (u - f < f + 1.0 - u ? u - f : f + 1.0 - u) * h;
+        if (gap < cm) cm = gap;
+        if (!(f >= 0.0 && f < (double)res)) {
+            if (cell_margin) *cell_margin = cm;
+            nrm[0] = 0.0; nrm[1] = 1.0; nrm[2] = 0.0;
+            return INFINITY;
+        }
+        c[a] = (int64_t)f;
+    }
+    if (cell_margin) *cell_margin = cm;
+#define ORC_SDF_AT(i, j, k) ((double)sdf[((int64_t)(k) * res + (j)) * res + (i)])
+    double g[3];
+    for (int a = 0; a < 3; ++a) {
+        int64_t lo[3] = {c[0], c[1], c[2]}, hi[3] = {c[0], c[1], c[2]};
+        if (lo[a] > 0) lo[a] -= 1;
+        if (hi[a] < res - 1) hi[a] += 1;
+        const double span = (double)(hi[a] - lo[a]) * h;
+        g[a] = span > 0.0 ? (ORC_SDF_AT(hi[0], hi[1], hi[2]) - ORC_SDF_AT(lo[0], lo[1], lo[2])) / span : 0.0;
+    }
+    const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (gn > 0.0) { nrm[0] = g[0] / gn; nrm[1] = g[1] / gn; nrm[2] = g[2] / gn; }
+    else { nrm[0] = 0.0; nrm[1] = 1.0; nrm[2] = 0.0; }
+    const double d = ORC_SDF_AT(c[0], c[1], c[2]);
+#undef ORC_SDF_AT
+    return d;
+}
+
 /* ------------------------------------------- grid operation (Eq. 7, 11-19) */
 
 /* grid_v: n^3 x 3 output.  contact (optional, n^3): index of the tool whose
  * projection was applied, -1 otherwise.  margin (optional, n^3): distance of
  * this node's floating-point decisions from a branch point -- min over
- * |d - theta|, |v_n| (if in contact) and the gap to the second-closest tool;
- * +inf where no decision depends on the tool. */
+ * |d - theta|, |v_n| (if in contact), the gap to the second-closest tool and
+ * the distance of x_ref from a cell face of a sampled field (where the
+ * sample is within 2h of theta); +inf where no decision depends on the tool. */
 void orc_grid_update(const orc_params *p, const orc_tool *tools, int32_t ntools,
                      const double *grid_m, const double *grid_mv, double *grid_v,
                      int32_t *contact, double *margin)
@@ -364,7 +416,7 @@ void orc_grid_update(const orc_params *p, const orc_tool *tools, int32_t ntools,
                         v[a] = grid_mv[3 * I + a] / grid_m[I] + p->dt * p->gravity[a];  /* Eq. 7 + gravity */
                     if (ntools > 0) {
                         const double xw[3] = {i * dx, j * dx, k * dx};
-                        double dmin = INFINITY, d2 = INFINITY, nref_best[3] = {0, 0, 0};
+                        double dmin = INFINITY, d2 = INFINITY, nref_best[3] = {0, 0, 0}, cells = INFINITY;
                         int id = -1;
                         for (int t = 0; t < ntools; ++t) {
                             const orc_tool *tl = tools + t;
@@ -374,7 +426,12 @@ void orc_grid_update(const orc_params *p, const orc_tool *tools, int32_t ntools,
                                 for (int b = 0; b < 3; ++b) s += tl->R[3 * b + a] * (xw[b] - tl->T[b]);
                                 xr[a] = s;
                             }
-                            const double d = orc_sdf(tl->kind, tl->dims, xr, nr);
+                            double cm = INFINITY;
+                            const double d = tl->kind == 2 ? orc_sdf_sampled(tl->sdf, tl->res, tl->dims, tl->h, xr, nr, &cm)
+                                                           : orc_sdf(tl->kind, tl->dims, xr, nr);
+                            /* a neighbouring sample of a distance field differs by at most
+                               sqrt(3) h, so the cell decision matters only near contact */
+                            if (d < p->theta + 2.0 * tl->h && cm < cells) cells = cm;
                             if (d < dmin) {
                                 d2 = dmin;
                                 dmin = d; id = t;
@@ -383,8 +440,9 @@ void orc_grid_update(const orc_params *p, const orc_tool *tools, int32_t ntools,
                                 d2 = d;
                             }
                         }
-                        mg = fabs(dmin - p->theta);
+                        mg = dmin < INFINITY ? fabs(dmin - p->theta) : INFINITY;
                         if (d2 < INFINITY && d2 - dmin < mg) mg = d2 - dmin;
+                        if (cells < mg) mg = cells;
                         if (dmin < p->theta) {
                             const orc_tool *tl = tools + id;
                             double nw[3], r[3], vco[3], vrel[3];

@@ -51,9 +51,9 @@ class Params(ct.Structure):
 
 
 class ToolFrame(ct.Structure):
-    _fields_ = [("kind", ct.c_int32), ("pad", ct.c_int32), ("dims", ct.c_double * 3),
+    _fields_ = [("kind", ct.c_int32), ("res", ct.c_int32), ("dims", ct.c_double * 3),
                 ("R", ct.c_double * 9), ("T", ct.c_double * 3), ("u", ct.c_double * 3),
-                ("w", ct.c_double * 3)]
+                ("w", ct.c_double * 3), ("h", ct.c_double), ("sdf", ct.POINTER(ct.c_float))]
 
 
 class Counters(ct.Structure):
@@ -84,6 +84,8 @@ def lib():
             L.orc_tool_frames.argtypes = [ct.c_int32, _D, _D, _D, ct.c_int32, ct.c_double, TF]
             L.orc_sdf.argtypes = [ct.c_int32, _D, _D, _D]
             L.orc_sdf.restype = ct.c_double
+            L.orc_sdf_sampled.argtypes = [ct.POINTER(ct.c_float), ct.c_int32, _D, ct.c_double, _D, _D, _D]
+            L.orc_sdf_sampled.restype = ct.c_double
             L.orc_grid_update.argtypes = [P, TF, ct.c_int32, _D, _D, _D,
                                           ct.POINTER(ct.c_int32), _D]
             L.orc_g2p.argtypes = [P, _D, ct.c_int64, _D, _D, _D, _D, CN]
@@ -194,14 +196,44 @@ def sdf(kind, dims, p):
     return d, n
 
 
-def tool_frames(shape, pose0, pose1, nsub, dt):
-    """Frames for one tool over one call of nsub sub-steps (see the C file)."""
+def _field_arrays(field):
+    samples = np.ascontiguousarray(field.samples, dtype=np.float32)
+    res = samples.shape[0]
+    assert samples.shape == (res, res, res)
+    return samples, res, _f64(field.origin, (3,)), float(field.h)
+
+
+def sdf_sampled(field, p):
+    """Sampled distance field lookup (Eqs. 12-14): (distance, unit normal,
+    distance of p from the nearest cell face)."""
+    samples, res, origin, h = _field_arrays(field)
+    p = _f64(p, (3,))
+    n = np.zeros(3)
+    cm = np.zeros(1)
+    d = lib().orc_sdf_sampled(samples.ctypes.data_as(ct.POINTER(ct.c_float)), res, _dp(origin), h,
+                              _dp(p), _dp(n), _dp(cm))
+    return d, n, float(cm[0])
+
+
+def tool_frames(shape, pose0, pose1, nsub, dt, field=None):
+    """Frames for one tool over one call of nsub sub-steps (see the C file).
+    A sampled tool (shape[0] == 2) takes its samples, origin and spacing from
+    field; the returned array keeps the samples alive."""
     shape = np.asarray(shape, dtype=np.float64)
     kind = int(shape[0])
     dims = _f64(shape[1:4])
+    if kind == 2:
+        samples, res, dims, h = _field_arrays(field)
     arr = (ToolFrame * nsub)()
     lib().orc_tool_frames(kind, _dp(dims), _dp(_f64(pose0, (6,))), _dp(_f64(pose1, (6,))),
                           int(nsub), float(dt), arr)
+    if kind == 2:
+        ptr = samples.ctypes.data_as(ct.POINTER(ct.c_float))
+        for k in range(nsub):
+            arr[k].res = res
+            arr[k].h = h
+            arr[k].sdf = ptr
+        arr._keep = [samples]
     return arr
 
 
@@ -215,11 +247,14 @@ def frames_for_steps(tools, s0, nsub, dt, call_len=None):
     call_len = call_len or nsub
     nt = len(tools)
     out = (ToolFrame * (nsub * nt))()
+    out._keep = []
     s = s0
     while s < s0 + nsub:
         m = min(call_len, s0 + nsub - s)
         for t, tool in enumerate(tools):
-            fr = tool_frames(tool.shape, tool.pose(s - 1), tool.pose(s + m - 1), m, dt)
+            fr = tool_frames(tool.shape, tool.pose(s - 1), tool.pose(s + m - 1), m, dt,
+                             getattr(tool, "field", None))
+            out._keep.append(getattr(fr, "_keep", None))
             for k in range(m):
                 ct.memmove(ct.byref(out, ((s - s0 + k) * nt + t) * ct.sizeof(ToolFrame)),
                            ct.byref(fr, k * ct.sizeof(ToolFrame)), ct.sizeof(ToolFrame))

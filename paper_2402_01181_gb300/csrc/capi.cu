@@ -75,6 +75,7 @@ void qmatrix(const Quat &q, double R[9]) {
 
 struct HostTool {
     int kind = MPM_TOOL_NONE;
+    int field = -1;                       // MPM_TOOL_SAMPLED: index into mpm_handle::fields
     double dims[3] = {0, 0, 0};
     double cur[6] = {0, 0, 0, 0, 0, 0};   // pose at the end of the last sub-step taken
     double tgt[6] = {0, 0, 0, 0, 0, 0};   // pose at the end of the next call
@@ -83,6 +84,14 @@ struct HostTool {
 struct Alloc {
     void *p;
     size_t bytes;
+};
+
+// A sampled distance field registered with mpm_add_sampled_field.
+struct HostField {
+    const float *d = nullptr;   // res^3 samples in handle-owned device memory
+    int res = 0;
+    double origin[3] = {0, 0, 0};
+    double h = 0;
 };
 
 }  // namespace
@@ -122,6 +131,7 @@ struct mpm_handle {
     cudaEvent_t ev_err = nullptr, ev_frames = nullptr;
     bool err_pending = false;
     std::vector<HostTool> tools;         // n_envs x MPM_MAX_TOOLS
+    std::vector<HostField> fields;       // sampled distance fields, shared by every environment
     // per-environment material
     std::vector<double> env_E, env_nu, env_rho, env_vol;
     std::vector<EnvParams> envp_host;
@@ -218,9 +228,22 @@ void fill_frames(mpm_handle *h, int first, int nsub, int total, int tstride, Too
             const Quat dq = qmul(q1, Quat{q0.w, -q0.x, -q0.y, -q0.z});
             double phi[3];
             qlog_rotvec(dq, phi);
-            double reach = tl.kind == MPM_TOOL_CAPSULE ? tl.dims[0] + tl.dims[1]
-                                                       : std::sqrt(tl.dims[0] * tl.dims[0] + tl.dims[1] * tl.dims[1] +
-                                                                   tl.dims[2] * tl.dims[2]);
+            const HostField *fd = tl.kind == MPM_TOOL_SAMPLED ? &h->fields[(size_t)tl.field] : nullptr;
+            double reach = 0.0;
+            if (tl.kind == MPM_TOOL_CAPSULE) {
+                reach = tl.dims[0] + tl.dims[1];
+            } else if (tl.kind == MPM_TOOL_BOX) {
+                reach = std::sqrt(tl.dims[0] * tl.dims[0] + tl.dims[1] * tl.dims[1] + tl.dims[2] * tl.dims[2]);
+            } else if (fd) {   // farthest corner of the sampled volume from the tool origin
+                for (int c = 0; c < 8; ++c) {
+                    double r2 = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        const double q = fd->origin[a] + ((c >> a) & 1 ? fd->res * fd->h : 0.0);
+                        r2 += q * q;
+                    }
+                    reach = std::max(reach, std::sqrt(r2));
+                }
+            }
             reach += std::max(0.0, (double)h->cfg.theta);
             reach = reach * 1.001 + 1e-6;
             for (int k = 0; k < nsub; ++k) {
@@ -237,7 +260,12 @@ void fill_frames(mpm_handle *h, int first, int nsub, int total, int tstride, Too
                     f.T[a] = (float)(tl.cur[a] + s * (tl.tgt[a] - tl.cur[a]));
                     f.u[a] = (float)((tl.tgt[a] - tl.cur[a]) / span);
                     f.w[a] = (float)(phi[a] / span);
-                    f.dims[a] = (float)tl.dims[a];
+                    f.dims[a] = (float)(fd ? fd->origin[a] : tl.dims[a]);
+                }
+                if (fd) {
+                    f.res = fd->res;
+                    f.inv_h = (float)(1.0 / fd->h);
+                    f.sdf = fd->d;
                 }
                 f.reach2 = (float)(reach * reach);
             }
@@ -607,14 +635,24 @@ mpm_status set_tool_impl(mpm_handle *h, int32_t env, int32_t tool_id, const doub
         t = HostTool();
         return MPM_OK;
     }
-    if (kind != MPM_TOOL_CAPSULE && kind != MPM_TOOL_BOX) return fail(MPM_ERR_ARG, "unknown tool kind %d", kind);
+    if (kind != MPM_TOOL_CAPSULE && kind != MPM_TOOL_BOX && kind != MPM_TOOL_SAMPLED)
+        return fail(MPM_ERR_ARG, "unknown tool kind %d", kind);
     for (int i = 0; i < 6; ++i)
         if (!std::isfinite(pose[i])) return fail(MPM_ERR_ARG, "non-finite pose");
-    for (int i = 1; i < 4; ++i)
-        if (!(shape[i] >= 0.f) || !std::isfinite(shape[i])) return fail(MPM_ERR_ARG, "shape sizes must be finite and >= 0");
+    int field = -1;
+    if (kind == MPM_TOOL_SAMPLED) {
+        if (!(shape[1] >= 0.f) || shape[1] != std::floor(shape[1]) || shape[1] >= (float)h->fields.size())
+            return fail(MPM_ERR_ARG, "shape[1] = %g is not a registered sampled field", (double)shape[1]);
+        field = (int)shape[1];
+    } else {
+        for (int i = 1; i < 4; ++i)
+            if (!(shape[i] >= 0.f) || !std::isfinite(shape[i]))
+                return fail(MPM_ERR_ARG, "shape sizes must be finite and >= 0");
+    }
     const bool fresh = t.kind == MPM_TOOL_NONE;
     t.kind = kind;
-    for (int a = 0; a < 3; ++a) t.dims[a] = shape[1 + a];
+    t.field = field;
+    for (int a = 0; a < 3; ++a) t.dims[a] = kind == MPM_TOOL_SAMPLED ? 0.0 : shape[1 + a];
     for (int i = 0; i < 6; ++i) {
         t.tgt[i] = pose[i];
         if (fresh) t.cur[i] = pose[i];
@@ -664,6 +702,35 @@ mpm_status mpm_set_env_tool_pose(mpm_handle *h, int32_t env, int32_t tool_id, co
 mpm_status mpm_set_tool_pose(mpm_handle *h, int32_t tool_id, const double pose[6], const float shape[8]) {
     if (!h) return fail(MPM_ERR_ARG, "NULL handle");
     return set_tool_impl(h, 0, tool_id, pose, shape);
+}
+
+mpm_status mpm_add_sampled_field(mpm_handle *h, int32_t res, const double origin[3], double spacing,
+                                 const float *samples, int on_device, int32_t *field_id) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (!origin || !samples || !field_id) return fail(MPM_ERR_ARG, "NULL origin, samples or field_id");
+    if (res < 1 || res > MPM_MAX_FIELD_RES) return fail(MPM_ERR_ARG, "res = %d outside [1, %d]", res, MPM_MAX_FIELD_RES);
+    if (!(spacing > 0.0) || !std::isfinite(spacing)) return fail(MPM_ERR_ARG, "spacing must be finite and > 0");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(origin[a])) return fail(MPM_ERR_ARG, "non-finite origin");
+    if (h->fields.size() >= (size_t)MPM_MAX_FIELDS) return fail(MPM_ERR_CAPACITY, "at most %d sampled fields", MPM_MAX_FIELDS);
+    const size_t count = (size_t)res * res * res;
+    if (!on_device)
+        for (size_t i = 0; i < count; ++i)
+            if (std::isnan(samples[i])) return fail(MPM_ERR_ARG, "sample %zu is NaN", i);
+    float *d = nullptr;
+    if ((st = dalloc_t(h, &d, count)) != MPM_OK) return st;
+    CK(cudaMemcpyAsync(d, samples, count * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    HostField f;
+    f.d = d;
+    f.res = res;
+    for (int a = 0; a < 3; ++a) f.origin[a] = origin[a];
+    f.h = spacing;
+    h->fields.push_back(f);
+    *field_id = (int32_t)(h->fields.size() - 1);
+    return MPM_OK;
 }
 
 mpm_status mpm_step(mpm_handle *h, int32_t n_substeps) {

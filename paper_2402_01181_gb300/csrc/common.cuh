@@ -50,10 +50,14 @@ struct __align__(16) ToolFrame {
     float T[3];
     float u[3];       // linear velocity of T
     float w[3];       // angular velocity
-    float dims[3];    // capsule: (radius, half-length, -); box: half extents
+    float dims[3];    // capsule: (radius, half-length, -); box: half extents;
+                      // sampled: tool-frame position o of sample (0, 0, 0)
     float reach2;     // squared radius beyond which the node is surely not in contact
-    int kind;         // 0 capsule, 1 box, -1 none
-    int pad[3];
+    int kind;         // 0 capsule, 1 box, 2 sampled distance field, -1 none
+    int res;          // sampled: samples per axis
+    float inv_h;      // sampled: 1 / sample spacing h
+    const float *sdf; // sampled: res^3 distances, x fastest; sample (i, j, k) is the
+                      // distance at o + h (i, j, k)
 };
 static_assert(sizeof(ToolFrame) == 28 * 4, "ToolFrame layout");
 
@@ -172,6 +176,36 @@ __device__ __forceinline__ void kirchhoff(const float F[9], float mu, float lam,
     t[5] = mu * bb22 + iso;
 }
 
+// Sampled distance field of Eqs. 12-14.  The cell index of a tool-frame
+// point is floor((p - o) / h) per axis (Eq. 12 indexes by x_ref / h); the
+// distance is that sample, the normal the central difference of the
+// neighbouring samples (Eq. 14; one-sided at the faces of the volume),
+// normalised.  Points outside the sampled volume are not in contact.
+// Returns (distance, normal).  Kept out of line: it is taken only for nodes
+// near a sampled tool and would otherwise raise the register count of every
+// kernel that runs the grid operation.
+static __device__ __noinline__ float4 sampled_sdf(const float *sdf, int res, float inv_h, float ox, float oy, float oz,
+                                           float px, float py, float pz) {
+    const float ux = floorf((px - ox) * inv_h), uy = floorf((py - oy) * inv_h), uz = floorf((pz - oz) * inv_h);
+    const float top = (float)res;
+    if (!(ux >= 0.f && uy >= 0.f && uz >= 0.f && ux < top && uy < top && uz < top))
+        return make_float4(3.0e38f, 0.f, 1.f, 0.f);
+    const int i = (int)ux, j = (int)uy, k = (int)uz;
+    const size_t r = (size_t)res;
+    auto at = [&](int a, int b, int c) { return __ldg(&sdf[((size_t)c * r + b) * r + a]); };
+    const int im = max(i - 1, 0), ip = min(i + 1, res - 1);
+    const int jm = max(j - 1, 0), jp = min(j + 1, res - 1);
+    const int km = max(k - 1, 0), kp = min(k + 1, res - 1);
+    // differences over 2 samples inside, 1 at a face; the common factor 1/h drops out
+    const float gx = (at(ip, j, k) - at(im, j, k)) / (float)max(ip - im, 1);
+    const float gy = (at(i, jp, k) - at(i, jm, k)) / (float)max(jp - jm, 1);
+    const float gz = (at(i, j, kp) - at(i, j, km)) / (float)max(kp - km, 1);
+    const float g2 = gx * gx + gy * gy + gz * gz;
+    if (!(g2 > 0.f)) return make_float4(at(i, j, k), 0.f, 1.f, 0.f);
+    const float il = 1.0f / sqrtf(g2);
+    return make_float4(at(i, j, k), gx * il, gy * il, gz * il);
+}
+
 // Signed distance of a tool-frame point to a capsule (axis along y) or a box
 // and the outward unit normal there (analytic stand-in for Eqs. 12-14).
 __device__ __forceinline__ float tool_sdf(int kind, const float *dims, float px, float py, float pz,
@@ -232,8 +266,13 @@ __device__ __forceinline__ float3 grid_node_update(float m, float mvx, float mvy
             const float px = tf.R[0] * rx + tf.R[3] * ry + tf.R[6] * rz;
             const float py = tf.R[1] * rx + tf.R[4] * ry + tf.R[7] * rz;
             const float pz = tf.R[2] * rx + tf.R[5] * ry + tf.R[8] * rz;
-            float nx, ny, nz;
-            const float d = tool_sdf(tf.kind, tf.dims, px, py, pz, nx, ny, nz);
+            float nx, ny, nz, d;
+            if (tf.kind == 2) {
+                const float4 s = sampled_sdf(tf.sdf, tf.res, tf.inv_h, tf.dims[0], tf.dims[1], tf.dims[2], px, py, pz);
+                d = s.x; nx = s.y; ny = s.z; nz = s.w;
+            } else {
+                d = tool_sdf(tf.kind, tf.dims, px, py, pz, nx, ny, nz);
+            }
             if (d < dmin) { dmin = d; id = t; nbx = nx; nby = ny; nbz = nz; }
         }
         if (id >= 0 && dmin < P.theta) {

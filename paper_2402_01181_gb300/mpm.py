@@ -33,6 +33,9 @@ MPM_PIPELINE_SPLIT = 1
 MPM_TOOL_NONE = -1
 MPM_TOOL_CAPSULE = 0
 MPM_TOOL_BOX = 1
+MPM_TOOL_SAMPLED = 2
+MPM_MAX_FIELDS = 16
+MPM_MAX_FIELD_RES = 1024
 
 STATUS_NAMES = {0: "MPM_OK", -1: "MPM_ERR_ARG", -2: "MPM_ERR_ALLOC", -3: "MPM_ERR_CUDA", -4: "MPM_ERR_NUMERIC",
                 -5: "MPM_ERR_DOMAIN", -6: "MPM_ERR_TIMEOUT", -7: "MPM_ERR_STATE", -8: "MPM_ERR_CAPACITY",
@@ -78,6 +81,8 @@ SIGNATURES = [
     ("mpm_read_order", ct.c_int, [ct.c_void_p, _U32P, _U32P]),
     ("mpm_block_sort_noalloc", ct.c_int, [ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_void_p, ct.c_void_p,
                                           ct.c_void_p]),
+    ("mpm_add_sampled_field", ct.c_int, [ct.c_void_p, ct.c_int32, _DP, ct.c_double, ct.c_void_p, ct.c_int,
+                                         ct.POINTER(ct.c_int32)]),
 ]
 
 
@@ -114,6 +119,7 @@ mpm_read_grid = lib.mpm_read_grid
 mpm_grid_velocity = lib.mpm_grid_velocity
 mpm_read_order = lib.mpm_read_order
 mpm_block_sort_noalloc = lib.mpm_block_sort_noalloc
+mpm_add_sampled_field = lib.mpm_add_sampled_field
 
 
 def mpm_last_error() -> str:
@@ -169,6 +175,7 @@ class Sim:
         dev = torch.cuda.current_device()
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
         self._keep = []
+        self._fields = {}
         if use_torch_allocator:
             def _alloc(nbytes, stream, ctx):
                 try:
@@ -231,14 +238,44 @@ class Sim:
     def set_env_material(self, env, E, nu, rho):
         check(mpm_set_env_material(self.h, int(env), float(E), float(nu), float(rho)))
 
-    def set_env_tool(self, env, tool_id, pose, shape):
+    def add_field(self, samples, origin, spacing) -> int:
+        """Register a sampled distance field (res^3 samples, x fastest) and
+        return its id for tools of kind MPM_TOOL_SAMPLED."""
+        o = np.ascontiguousarray(np.asarray(origin, dtype=np.float64).reshape(3))
+        fid = ct.c_int32()
+        if hasattr(samples, "is_cuda") and samples.is_cuda:
+            t = samples.contiguous().float()
+            res = int(round(t.numel() ** (1.0 / 3.0)))
+            assert res ** 3 == t.numel(), "samples must hold res^3 values"
+            check(mpm_add_sampled_field(self.h, res, o.ctypes.data_as(_DP), float(spacing),
+                                        ct.c_void_p(t.data_ptr()), 1, ct.byref(fid)))
+        else:
+            a = np.ascontiguousarray(np.asarray(samples, dtype=np.float32))
+            res = int(round(a.size ** (1.0 / 3.0)))
+            assert res ** 3 == a.size, "samples must hold res^3 values"
+            check(mpm_add_sampled_field(self.h, res, o.ctypes.data_as(_DP), float(spacing),
+                                        a.ctypes.data_as(ct.c_void_p), 0, ct.byref(fid)))
+        return int(fid.value)
+
+    def _shape_for(self, shape, field):
+        s = np.array(np.asarray(shape, dtype=np.float32).reshape(8))
+        if field is not None and int(s[0]) == MPM_TOOL_SAMPLED:
+            key = id(field)
+            if key not in self._fields:
+                self._fields[key] = (self.add_field(field.samples, field.origin, field.h), field)
+            s[1] = self._fields[key][0]
+        return s
+
+    def set_env_tool(self, env, tool_id, pose, shape, field=None):
+        """Tool pose and shape; a sampled shape (kind MPM_TOOL_SAMPLED) takes
+        its distances from `field` (a scenes.SampledField, registered once)."""
         p = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(6))
-        s = np.ascontiguousarray(np.asarray(shape, dtype=np.float32).reshape(8))
+        s = self._shape_for(shape, field)
         check(mpm_set_env_tool_pose(self.h, int(env), int(tool_id), p.ctypes.data_as(_DP), s.ctypes.data_as(_FP)))
 
-    def set_tool(self, tool_id, pose, shape):
+    def set_tool(self, tool_id, pose, shape, field=None):
         p = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(6))
-        s = np.ascontiguousarray(np.asarray(shape, dtype=np.float32).reshape(8))
+        s = self._shape_for(shape, field)
         check(mpm_set_tool_pose(self.h, int(tool_id), p.ctypes.data_as(_DP), s.ctypes.data_as(_FP)))
 
     def step(self, n_substeps=1):
@@ -293,5 +330,5 @@ def sim_from_scene(sc, pipeline=MPM_PIPELINE_FUSED, max_particles=None, load=Tru
     if load:
         s.load(sc.x, sc.particle_volume, sc.v, sc.F, sc.C)
         for t, tool in enumerate(sc.tools):
-            s.set_tool(t, tool.pose(-1), tool.shape)
+            s.set_tool(t, tool.pose(-1), tool.shape, tool.field)
     return s

@@ -14,6 +14,7 @@ Random numbers come from numpy's PCG64 generator with an explicit seed.
 """
 from __future__ import annotations
 
+import functools
 from dataclasses import dataclass, field
 from typing import Callable, List, Optional, Sequence
 
@@ -22,6 +23,21 @@ import numpy as np
 # Tool shape kinds, matching the `shape[0]` code of the C ABI.
 CAPSULE = 0
 BOX = 1
+SAMPLED = 2
+
+
+@dataclass
+class SampledField:
+    """A distance field precomputed on a cubic lattice in a tool's reference
+    frame (the offline SDF of Sec. III-C): samples[k, j, i] is the distance
+    at origin + h * (i, j, k); res = samples.shape[0]."""
+    samples: np.ndarray                # (res, res, res) float32, x fastest
+    origin: np.ndarray                 # (3,) float64
+    h: float
+
+    @property
+    def res(self) -> int:
+        return int(self.samples.shape[0])
 
 
 @dataclass
@@ -30,12 +46,13 @@ class Tool:
 
     shape: 8 floats -- [kind, a, b, c, 0, 0, 0, 0]; capsule: a = radius,
     b = half-length of the axis segment along local y; box: (a, b, c) = half
-    extents.  pose(s) returns the 6-vector (T xyz, rotation vector xyz) the
-    tool has at the END of global sub-step s (s = 0, 1, ...); pose(-1) is the
-    starting pose.
+    extents; sampled: the distances come from `field`.  pose(s) returns the
+    6-vector (T xyz, rotation vector xyz) the tool has at the END of global
+    sub-step s (s = 0, 1, ...); pose(-1) is the starting pose.
     """
     shape: np.ndarray
     pose: Callable[[int], np.ndarray]
+    field: Optional[SampledField] = None
 
 
 @dataclass
@@ -140,6 +157,71 @@ def box_shape(hx, hy, hz):
     return s
 
 
+def sampled_shape():
+    s = np.zeros(8, dtype=np.float32)
+    s[0] = SAMPLED
+    return s
+
+
+# --------------------------------------------------------------------------
+# Rasterised tool geometry.  The paper's tool meshes are not distributed, so
+# sampled fields are made from simple solids: the distance to a union of
+# capsules and boxes (exact outside the union, a bound inside it).
+# --------------------------------------------------------------------------
+
+def _capsule_distance(p, radius, half_length):
+    c = np.clip(p[..., 1], -half_length, half_length)
+    q = p.copy()
+    q[..., 1] -= c
+    return np.linalg.norm(q, axis=-1) - radius
+
+
+def _box_distance(p, center, half):
+    q = np.abs(p - np.asarray(center)) - np.asarray(half)
+    outside = np.linalg.norm(np.maximum(q, 0.0), axis=-1)
+    inside = np.minimum(q.max(axis=-1), 0.0)
+    return outside + inside
+
+
+def rasterize(distance: Callable[[np.ndarray], np.ndarray], origin, h: float, res: int) -> SampledField:
+    """Sample distance(p) at origin + h (i, j, k), one z slab at a time."""
+    origin = np.asarray(origin, dtype=np.float64)
+    out = np.empty((res, res, res), dtype=np.float32)
+    ii = np.arange(res, dtype=np.float64)
+    gy, gx = np.meshgrid(ii, ii, indexing="ij")
+    for k in range(res):
+        p = np.stack([origin[0] + h * gx, origin[1] + h * gy, np.full_like(gx, origin[2] + h * k)], axis=-1)
+        out[k] = distance(p)
+    return SampledField(out, origin, float(h))
+
+
+@functools.lru_cache(maxsize=4)
+def grasper_field(res: int = 256, radius: float = 0.012, half_length: float = 0.12,
+                  jaw=(0.006, 0.02, 0.012), gap: float = 0.008) -> SampledField:
+    """A grasper stand-in: a shaft (capsule along local y, centred at the
+    origin) ending in two parallel jaws (boxes of half extents `jaw`, 2*gap
+    apart in x) below its lower end.  The field covers the cube centred on
+    the solid's bounding box with a margin of 3.3 samples (a spacing that is
+    no simple fraction of a grid cell, so that grid nodes do not sit on
+    sample-cell faces)."""
+    jaw_y = -half_length - radius - jaw[1]
+    centers = [(gap + jaw[0], jaw_y, 0.0), (-gap - jaw[0], jaw_y, 0.0)]
+    lo_y = jaw_y - jaw[1]
+    hi_y = half_length + radius
+    side = max(hi_y - lo_y, 2 * (gap + 2 * jaw[0]), 2 * radius)
+    h = side / (res - 6.6)
+    mid_y = 0.5 * (lo_y + hi_y)
+    origin = np.array([-0.5 * side - 3.3 * h, mid_y - 0.5 * side - 3.3 * h, -0.5 * side - 3.3 * h])
+
+    def dist(p):
+        d = _capsule_distance(p, radius, half_length)
+        for c in centers:
+            d = np.minimum(d, _box_distance(p, c, jaw))
+        return d
+
+    return rasterize(dist, origin, h, res)
+
+
 # --------------------------------------------------------------------------
 # The workloads.  Sizes follow the paper's scale (30K particles, 64^3 grid,
 # rho = 1000 kg/m^3, Sec. IV) and the roofline sweep (1M / 8M particles).
@@ -201,9 +283,35 @@ def block8m(seed: int = 0) -> Scene:
     return _block(256, 100, seed, "block8m")
 
 
+def slab30k_sdf(seed: int = 0, res: int = 256) -> Scene:
+    """slab30k with the capsule replaced by a sampled grasper field (res^3
+    samples, the paper's 256 by default): its jaws press 0.05 m into the slab
+    over sub-steps 0-999, then it drags 0.10 m along +x while turning 0.3 rad
+    about its axis over sub-steps 1000-1999."""
+    sc = slab30k(seed)
+    field = grasper_field(res, radius=0.02, half_length=0.15, jaw=(0.012, 0.03, 0.02), gap=0.012)
+    tip = -field.origin[1] - 3.3 * field.h         # depth of the jaw tips below the origin
+    p0 = np.array([0.5013, 3.0 / 64 + 0.1 + 0.005 + tip, 0.4987, 0.0, 0.0, 0.0])
+    down = _linear_path(p0, [(1000, (0.0, -0.05, 0.0))])
+
+    def pose(s):
+        if s < 1000:
+            return down(s)
+        t = min((s + 1 - 1000) / 1000.0, 1.0)
+        out = down(999).copy()
+        out[0] += 0.10 * t
+        out[4] = 0.3 * t
+        return out
+
+    sc.name = "slab30k_sdf"
+    sc.tools = [Tool(sampled_shape(), pose, field)]
+    return sc
+
+
 SCENES = {
     "cube8k": cube8k,
     "slab30k": slab30k,
+    "slab30k_sdf": slab30k_sdf,
     "block1m": block1m,
     "block8m": block8m,
 }

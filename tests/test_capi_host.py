@@ -57,5 +57,8 @@ def test_argument_validation_without_gpu(lib):
         st = lib.mpm_create(ct.byref(cfg), None, lib.mpm_alloc_fn(), lib.mpm_free_fn(), None, ct.byref(h))
         assert st == lib.MPM_ERR_ARG, bad
     assert lib.mpm_step(None, 1) == lib.MPM_ERR_ARG
+    fid = ct.c_int32(-1)
+    o = (ct.c_double * 3)()
+    assert lib.mpm_add_sampled_field(None, 4, o, 0.1, None, 0, ct.byref(fid)) == lib.MPM_ERR_ARG
     assert lib.mpm_destroy(None) == lib.MPM_ERR_ARG
     assert lib.mpm_read_particles(None, None, None, None, None, 0) == lib.MPM_ERR_ARG

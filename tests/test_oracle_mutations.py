@@ -31,6 +31,16 @@ MUTATIONS = {
     "tool velocity drops spin": ("vco[0] = tl->u[0] + tl->w[1] * r[2] - tl->w[2] * r[1];", "vco[0] = tl->u[0];"),
     "z-buffer picks farthest": ("if (d < dmin) {", "if (d > dmin || dmin == INFINITY) {"),
     "walls ignored": ("v[0] = v[1] = v[2] = 0.0;          /* sticky walls */", ";"),
+    "sampled index rounds": ("const double f = floor(u);", "const double f = floor(u + 0.5);"),
+    "sampled axis order": ("#define ORC_SDF_AT(i, j, k) ((double)sdf[((int64_t)(k) * res + (j)) * res + (i)])",
+                           "#define ORC_SDF_AT(i, j, k) ((double)sdf[((int64_t)(i) * res + (j)) * res + (k)])"),
+    "sampled normal not normalised": ("if (gn > 0.0) { nrm[0] = g[0] / gn; nrm[1] = g[1] / gn; nrm[2] = g[2] / gn; }",
+                                      "if (gn > 0.0) { nrm[0] = g[0]; nrm[1] = g[1]; nrm[2] = g[2]; }"),
+    "sampled difference reversed": ("(ORC_SDF_AT(hi[0], hi[1], hi[2]) - ORC_SDF_AT(lo[0], lo[1], lo[2])) / span",
+                                    "(ORC_SDF_AT(lo[0], lo[1], lo[2]) - ORC_SDF_AT(hi[0], hi[1], hi[2])) / span"),
+    "sampled faces not one-sided": ("const double span = (double)(hi[a] - lo[a]) * h;", "const double span = 2.0 * h;"),
+    "sampled outside counts as contact": ("            return INFINITY;\n        }\n        c[a] = (int64_t)f;",
+                                          "            return -1.0;\n        }\n        c[a] = (int64_t)f;"),
     "block key axis order": ("keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));", "keys[q] = (uint32_t)(b[2] + nb * (b[1] + nb * b[0]));"),
 }
 

@@ -485,3 +485,128 @@ def test_inverted_particles_are_counted():
     st = O.State(x, None, None, F)
     O.p2g(prm, st)
     assert st.counters.j_clamped == 1
+
+
+# ------------------------------------------------- sampled distance fields
+
+def _field(fn, origin, h, res):
+    """Samples fn at origin + h (i, j, k), x fastest -- written out here so
+    the pins do not lean on the scene module's rasteriser."""
+    out = np.empty((res, res, res), dtype=np.float32)
+    for k in range(res):
+        for j in range(res):
+            for i in range(res):
+                out[k, j, i] = fn(np.asarray(origin) + h * np.array([i, j, k], dtype=np.float64))
+    return scenes.SampledField(out, np.asarray(origin, dtype=np.float64), h)
+
+
+def test_sampled_field_reads_the_lower_sample_of_a_linear_field():
+    """Eq. 12 reads the sample at floor((x_ref - o) / h); Eq. 14's central
+    difference of a linear field is its exact gradient, also one-sided at the
+    faces, so the unit normal is a / |a| everywhere inside the field; outside
+    it there is no contact (+inf)."""
+    a = np.array([0.3, -1.7, 0.9])
+    c = 0.05
+    o = np.array([-0.125, 0.0625, -0.25])                # powers of two: sample positions are exact
+    h, res = 1.0 / 64, 10
+    fld = _field(lambda q: a @ q + c, o, h, res)
+    rng = np.random.default_rng(13)
+    unit = a / np.linalg.norm(a)
+    pts = [o + h * res * rng.random(3) for _ in range(200)]
+    for ax in range(3):                                    # first and last cell on each axis
+        for cell in (0, res - 1):
+            p = o + h * res * rng.random(3)
+            p[ax] = o[ax] + h * (cell + 0.37)
+            pts.append(p)
+    for p in pts:
+        d, nrm, _ = O.sdf_sampled(fld, p)
+        corner = o + h * np.floor((p - o) / h)
+        assert abs(d - (a @ corner + c)) < 1e-6, p
+        assert np.allclose(nrm, unit, atol=1e-6), (p, nrm)
+    for i in range(res):                                   # exactly on a sample, and just below it
+        p = o + h * np.array([i, 3, 5], dtype=np.float64)
+        assert O.sdf_sampled(fld, p)[0] == pytest.approx(a @ p + c, abs=1e-6)
+        if i > 0:
+            q = p.copy()
+            q[0] -= 1e-12
+            assert O.sdf_sampled(fld, q)[0] == pytest.approx(a @ (p - h * np.array([1, 0, 0])) + c, abs=1e-6)
+    for ax in range(3):
+        for p_ax in (o[ax] - 1e-9, o[ax] + h * res, o[ax] + h * res + 0.3):
+            p = o + 0.5 * h * res
+            p[ax] = p_ax
+            assert O.sdf_sampled(fld, p)[0] == np.inf
+
+
+def test_sampled_sphere_field_converges_to_the_sphere():
+    """A sampled sphere's distance is within sqrt(3) h of the exact one (the
+    field is 1-Lipschitz and the sample lies in the same cell), and its
+    central-difference normal points radially from that sample."""
+    R, h, res = 0.1, 0.3 / 24, 24
+    o = np.array([-0.15, -0.15, -0.15])
+    fld = _field(lambda q: np.linalg.norm(q) - R, o, h, res)
+    rng = np.random.default_rng(14)
+    for _ in range(300):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        p = u * rng.uniform(0.07, 0.13)
+        d, nrm, _ = O.sdf_sampled(fld, p)
+        assert abs(d - (np.linalg.norm(p) - R)) <= math.sqrt(3) * h + 1e-7
+        corner = o + h * np.floor((p - o) / h)              # the sample the normal is taken at
+        assert nrm @ (corner / np.linalg.norm(corner)) > 0.999
+
+
+def test_sampled_tool_contact_removes_the_normal_velocity():
+    """A static sampled tool whose field is the plane 2 (q_y - y0) (gradient
+    of length 2, so the normal must be normalised), turned about z by phi:
+    with mu = 0 a node moving into it keeps exactly its velocity minus the
+    component along the world normal R e_y; a separating node is untouched.
+    x_ref of the node is (0, -0.003, 0), well inside a cell."""
+    fld = _field(lambda q: 2.0 * (q[1] - 0.013), np.array([-0.0625] * 3), 1.0 / 128, 16)
+    prm = _params(n=8, friction=0.0)
+    node = np.array([0.5, 0.5, 0.5])
+    for phi in (0.0, 0.7, -2.1):
+        pose = np.zeros(6)
+        pose[5] = phi
+        R = O.rotvec_to_matrix(pose[3:]).reshape(3, 3)
+        pose[:3] = node - R @ np.array([0.0, -0.003, 0.0])
+        frames = O.tool_frames(scenes.sampled_shape(), pose, pose, 1, 1e-3, fld)
+        n_w = R @ np.array([0.0, 1.0, 0.0])
+        t_w = R @ np.array([1.0, 0.0, 0.2])
+        for v_in, touches in ((-0.5 * n_w + t_w, True), (0.4 * n_w + t_w, False)):
+            m, mv = _one_node_grid({"v_in": v_in})
+            gv, contact, _ = O.grid_update(prm, m, mv, frames, 1)
+            assert contact[4, 4, 4] == 0
+            want = v_in - (v_in @ n_w) * n_w if touches else v_in
+            assert np.allclose(gv[4, 4, 4], want, atol=1e-12), (phi, gv[4, 4, 4], want)
+
+
+def test_sampled_capsule_agrees_with_the_analytic_capsule():
+    """The grid operation with a sampled capsule (h = dx / 4) finds the same
+    contacts as with the analytic capsule wherever the analytic distance is
+    more than sqrt(3) h from the threshold."""
+    n, r, hl = 32, 0.06, 0.08
+    prm = _params(n=n, friction=0.3, theta=0.0)
+    h, res = (1.0 / n) / 4, 48
+    o = np.full(3, -0.5 * h * res) + np.array([0.0013, -0.0021, 0.0007])
+    dims = np.array([r, hl, 0.0])
+    fld = _field(lambda q: O.sdf(scenes.CAPSULE, dims, q)[0], o, h, res)
+    rng = np.random.default_rng(15)
+    pose = np.array([0.51, 0.49, 0.5, 0.3, -0.2, 0.5])
+    m = np.zeros((n, n, n))
+    mv = np.zeros((n, n, n, 3))
+    m[8:24, 8:24, 8:24] = 1.0
+    mv[8:24, 8:24, 8:24] = rng.normal(size=(16, 16, 16, 3))
+    fa = O.tool_frames(scenes.capsule_shape(r, hl), pose, pose, 1, 1e-3)
+    fs = O.tool_frames(scenes.sampled_shape(), pose, pose, 1, 1e-3, fld)
+    _, ca, _ = O.grid_update(prm, m, mv, fa, 1)
+    _, cs, _ = O.grid_update(prm, m, mv, fs, 1)
+    R = O.rotvec_to_matrix(pose[3:]).reshape(3, 3)
+    ii = np.argwhere(m > 0)
+    far = 0
+    for i, j, k in ii:
+        xr = R.T @ (np.array([i, j, k]) / n - pose[:3])
+        da = O.sdf(scenes.CAPSULE, dims, xr)[0]
+        if abs(da) > math.sqrt(3) * h:
+            far += 1
+            assert ca[i, j, k] == cs[i, j, k], (i, j, k, da)
+    assert far > 1000 and (ca == 0).sum() > 50
