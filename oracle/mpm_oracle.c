@@ -569,3 +569,346 @@ void orc_block_keys(int32_t n_grid, int64_t N, const float *x, uint32_t *keys)
         keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));
     }
 }
+
+/* ======================================================================
+ * Adjoint (reverse mode) of one sub-step.
+ *
+ * The paper does not differentiate its simulator (Sec. V names
+ * differentiable physics as future work); this is the plain derivative of
+ * orc_step, stage by stage in reverse order (G2P, grid operation, P2G),
+ * taken from the formulas above.  Every branch of the forward pass (m > 0,
+ * contact d < theta, approaching v_n < 0, the friction clamp, the z-buffer
+ * choice, walls, the stencil base) is held at the side the forward pass
+ * took, so the result is the derivative of the branch taken.  The distance
+ * d only selects branches and contributes no derivative; the sampled field
+ * is piecewise constant in x_ref and contributes none either.
+ * ====================================================================== */
+
+/* d w / d fx of orc_weights */
+static void weights_d(double fx, double *dw)
+{
+    dw[0] = -(1.5 - fx);
+    dw[1] = -2.0 * (fx - 1.0);
+    dw[2] = fx - 0.5;
+}
+
+/* Jacobian d n / d p (row-major: row = component of n) of the unit normal
+ * orc_sdf returns for analytic shapes; zero where that normal is constant
+ * (inside a box, on the capsule axis) and for sampled fields. */
+static void sdf_normal_jacobian(int32_t kind, const double *dims, const double *p, double *Jn)
+{
+    for (int i = 0; i < 9; ++i) Jn[i] = 0.0;
+    if (kind == 0) {
+        double c = p[1];
+        int side = 1;                   /* the closest axis point moves with p_y */
+        if (c > dims[1]) { c = dims[1]; side = 0; }
+        if (c < -dims[1]) { c = -dims[1]; side = 0; }
+        const double q[3] = {p[0], p[1] - c, p[2]};
+        const double L = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+        if (!(L > 0.0)) return;
+        const double u[3] = {q[0] / L, q[1] / L, q[2] / L};
+        const double D[3] = {1.0, side ? 0.0 : 1.0, 1.0};   /* d q / d p */
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Jn[3 * a + b] = ((a == b ? 1.0 : 0.0) - u[a] * u[b]) / L * D[b];
+        return;
+    }
+    if (kind == 1) {
+        double q[3], o[3], s[3], on = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            q[d] = fabs(p[d]) - dims[d];
+            o[d] = q[d] > 0.0 ? q[d] : 0.0;
+            s[d] = p[d] < 0.0 ? -1.0 : 1.0;
+            on += o[d] * o[d];
+        }
+        on = sqrt(on);
+        if (!(on > 0.0)) return;
+        for (int d = 0; d < 3; ++d)
+            for (int e = 0; e < 3; ++e)
+                if (q[d] > 0.0 && q[e] > 0.0)
+                    Jn[3 * d + e] = s[d] * s[e] * ((d == e ? 1.0 : 0.0) - o[d] * o[e] / (on * on)) / on;
+    }
+}
+
+/* Eq. 6 backwards: (dL/dmu, dL/dlam) -> (dL/dE, dL/dnu). */
+void orc_lame_vjp(double E, double nu, double mu_bar, double lam_bar, double *E_bar, double *nu_bar)
+{
+    const double D = (1.0 + nu) * (1.0 - 2.0 * nu);
+    *E_bar = mu_bar / (2.0 * (1.0 + nu)) + lam_bar * nu / D;
+    *nu_bar = -mu_bar * E / (2.0 * (1.0 + nu) * (1.0 + nu)) + lam_bar * E * (1.0 + 2.0 * nu * nu) / (D * D);
+}
+
+/* Reverse mode of orc_step.  x, v, C, F: the state at the START of the
+ * sub-step (left unchanged).  xb, vb, Cb, Fb: on entry the adjoint dL/d(state
+ * after the sub-step), on return dL/d(state before it).  lame_bar[2]
+ * accumulates dL/dmu, dL/dlam; tool_bar (ntools x 18: R row-major, T, u, w
+ * of each frame) accumulates dL/d(frame entries).  Returns -1 if scratch
+ * memory could not be allocated, else 0. */
+int orc_step_adjoint(const orc_params *p, const orc_tool *tools, int32_t ntools, int64_t N,
+                     const double *x, const double *v, const double *C, const double *F,
+                     double *xb, double *vb, double *Cb, double *Fb,
+                     double *lame_bar, double *tool_bar)
+{
+    const int n = p->n_grid;
+    const double dx = 1.0 / n, K = 4.0 / (dx * dx), dt = p->dt;
+    const int64_t nn = (int64_t)n * n * n;
+    const double mp = p->rho * p->V0;
+    double mu, lam;
+    orc_lame(p->E, p->nu, &mu, &lam);
+    double *gm = (double *)malloc(sizeof(double) * nn);
+    double *gmv = (double *)malloc(sizeof(double) * 3 * nn);
+    double *gv = (double *)malloc(sizeof(double) * 3 * nn);
+    double *gvb = (double *)calloc(3 * nn, sizeof(double));     /* dL/d(grid velocity) */
+    double *gmb = (double *)calloc(nn, sizeof(double));         /* dL/d(grid mass) */
+    double *gmvb = (double *)calloc(3 * nn, sizeof(double));    /* dL/d(grid momentum) */
+    if (!gm || !gmv || !gv || !gvb || !gmb || !gmvb) {
+        free(gm); free(gmv); free(gv); free(gvb); free(gmb); free(gmvb);
+        return -1;
+    }
+    /* the forward pass up to the grid velocities */
+    orc_p2g(p, N, x, v, C, F, gm, gmv, NULL);
+    orc_grid_update(p, tools, ntools, gm, gmv, gv, NULL, NULL);
+
+    /* ---- G2P (Eqs. 4, 8-10) backwards */
+    for (int64_t q = 0; q < N; ++q) {
+        const double *xp = x + 3 * q, *Fp = F + 9 * q;
+        int base[3];
+        double fx[3], w[3][3], dw[3][3];
+        stencil_base(p, xp, base, fx);
+        for (int d = 0; d < 3; ++d) { orc_weights(fx[d], w[d]); weights_d(fx[d], dw[d]); }
+        double B[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    const double wip = w[0][i] * w[1][j] * w[2][k];
+                    const double dpos[3] = {(i - fx[0]) * dx, (j - fx[1]) * dx, (k - fx[2]) * dx};
+                    const double *vi = gv + 3 * node_index(n, base[0] + i, base[1] + j, base[2] + k);
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) B[3 * a + b] += wip * vi[a] * dpos[b];
+                }
+        double Cn[9], IdtC[9];
+        for (int a = 0; a < 9; ++a) { Cn[a] = K * B[a]; IdtC[a] = ((a % 4 == 0) ? 1.0 : 0.0) + dt * Cn[a]; }
+        const double *xbo = xb + 3 * q, *vbo = vb + 3 * q, *Cbo = Cb + 9 * q, *Fbo = Fb + 9 * q;
+        double vbt[3], Cbt[9], Fbn[9], xbn[3];
+        for (int a = 0; a < 3; ++a) { vbt[a] = vbo[a] + dt * xbo[a]; xbn[a] = xbo[a]; }   /* x' = x + dt v' */
+        for (int a = 0; a < 3; ++a)                                                       /* F' = (I + dt C') F */
+            for (int b = 0; b < 3; ++b) {
+                double sF = 0.0, sC = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    sF += IdtC[3 * c + a] * Fbo[3 * c + b];
+                    sC += Fbo[3 * a + c] * Fp[3 * b + c];
+                }
+                Fbn[3 * a + b] = sF;
+                Cbt[3 * a + b] = Cbo[3 * a + b] + dt * sC;
+            }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    const double wip = w[0][i] * w[1][j] * w[2][k];
+                    const double gw[3] = {dw[0][i] * w[1][j] * w[2][k] * n, w[0][i] * dw[1][j] * w[2][k] * n,
+                                          w[0][i] * w[1][j] * dw[2][k] * n};        /* d w_ip / d x_p */
+                    const double dpos[3] = {(i - fx[0]) * dx, (j - fx[1]) * dx, (k - fx[2]) * dx};
+                    const int64_t I = node_index(n, base[0] + i, base[1] + j, base[2] + k);
+                    const double *vi = gv + 3 * I;
+                    double s = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        double cd = 0.0;
+                        for (int b = 0; b < 3; ++b) cd += Cbt[3 * a + b] * dpos[b];
+                        gvb[3 * I + a] += wip * (vbt[a] + K * cd);                /* Eqs. 8-9 */
+                        s += vi[a] * (vbt[a] + K * cd);
+                    }
+                    for (int d = 0; d < 3; ++d) xbn[d] += gw[d] * s;
+                    for (int b = 0; b < 3; ++b) {                                  /* d dpos / d x_p = -I */
+                        double cv = 0.0;
+                        for (int a = 0; a < 3; ++a) cv += Cbt[3 * a + b] * vi[a];
+                        xbn[b] -= K * wip * cv;
+                    }
+                }
+        for (int a = 0; a < 3; ++a) { xb[3 * q + a] = xbn[a]; vb[3 * q + a] = 0.0; }
+        for (int a = 0; a < 9; ++a) { Fb[9 * q + a] = Fbn[a]; Cb[9 * q + a] = 0.0; }
+    }
+
+    /* ---- grid operation (Eq. 7, gravity, Eqs. 11-19, walls) backwards */
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            for (int k = 0; k < n; ++k) {
+                const int64_t I = node_index(n, i, j, k);
+                if (!(gm[I] > 0.0)) continue;                      /* v = 0: no dependence */
+                const int b = p->bound;
+                if (i < b || j < b || k < b || i >= n - b || j >= n - b || k >= n - b) continue;
+                double vf[3], vbar[3];
+                for (int a = 0; a < 3; ++a) {
+                    vf[a] = gmv[3 * I + a] / gm[I] + dt * p->gravity[a];
+                    vbar[a] = gvb[3 * I + a];
+                }
+                if (ntools > 0) {
+                    const double xw[3] = {i * dx, j * dx, k * dx};
+                    double dmin = INFINITY, nref[3] = {0, 0, 0}, xref_best[3] = {0, 0, 0};
+                    int id = -1;
+                    for (int t = 0; t < ntools; ++t) {
+                        const orc_tool *tl = tools + t;
+                        double xr[3], nr[3];
+                        for (int a = 0; a < 3; ++a) {
+                            double s = 0.0;
+                            for (int c = 0; c < 3; ++c) s += tl->R[3 * c + a] * (xw[c] - tl->T[c]);
+                            xr[a] = s;
+                        }
+                        const double d = tl->kind == 2 ? orc_sdf_sampled(tl->sdf, tl->res, tl->dims, tl->h, xr, nr, NULL)
+                                                       : orc_sdf(tl->kind, tl->dims, xr, nr);
+                        if (d < dmin) {
+                            dmin = d; id = t;
+                            for (int a = 0; a < 3; ++a) { nref[a] = nr[a]; xref_best[a] = xr[a]; }
+                        }
+                    }
+                    if (dmin < p->theta) {
+                        const orc_tool *tl = tools + id;
+                        double nw[3], r[3], vco[3], vrel[3], vn = 0.0;
+                        for (int a = 0; a < 3; ++a) {
+                            nw[a] = 0.0;
+                            for (int c = 0; c < 3; ++c) nw[a] += tl->R[3 * a + c] * nref[c];
+                            r[a] = xw[a] - tl->T[a];
+                        }
+                        vco[0] = tl->u[0] + tl->w[1] * r[2] - tl->w[2] * r[1];
+                        vco[1] = tl->u[1] + tl->w[2] * r[0] - tl->w[0] * r[2];
+                        vco[2] = tl->u[2] + tl->w[0] * r[1] - tl->w[1] * r[0];
+                        for (int a = 0; a < 3; ++a) { vrel[a] = vf[a] - vco[a]; vn += vrel[a] * nw[a]; }
+                        if (vn < 0.0) {
+                            double vt[3], vtn = 0.0;
+                            for (int a = 0; a < 3; ++a) { vt[a] = vrel[a] - vn * nw[a]; vtn += vt[a] * vt[a]; }
+                            vtn = sqrt(vtn);
+                            double scale = 0.0;
+                            if (vtn > 0.0) {
+                                const double s = vtn + p->friction * vn;
+                                scale = s > 0.0 ? s / vtn : 0.0;
+                            }
+                            /* v' = scale vt + vco */
+                            double vtb[3] = {0, 0, 0}, vnb = 0.0, nwb[3], vrelb[3], vcob[3];
+                            if (scale > 0.0) {
+                                double scb = 0.0;
+                                for (int a = 0; a < 3; ++a) { vtb[a] = scale * vbar[a]; scb += vbar[a] * vt[a]; }
+                                /* scale = 1 + mu_f vn / |vt| */
+                                vnb += p->friction * scb / vtn;
+                                const double vtnb = -p->friction * vn * scb / (vtn * vtn);
+                                for (int a = 0; a < 3; ++a) vtb[a] += vtnb * vt[a] / vtn;
+                            }
+                            /* vt = vrel - vn nw */
+                            double vtb_n = 0.0;
+                            for (int a = 0; a < 3; ++a) { vrelb[a] = vtb[a]; vtb_n += vtb[a] * nw[a]; nwb[a] = -vn * vtb[a]; }
+                            vnb -= vtb_n;
+                            /* vn = vrel . nw */
+                            for (int a = 0; a < 3; ++a) { vrelb[a] += vnb * nw[a]; nwb[a] += vnb * vrel[a]; }
+                            /* vrel = v - vco, and v' carries + vco */
+                            for (int a = 0; a < 3; ++a) vcob[a] = vbar[a] - vrelb[a];
+                            double *tb = tool_bar + 18 * id;           /* R[9], T[3], u[3], w[3] */
+                            /* vco = u + w x r, r = x - T */
+                            double rb[3];
+                            for (int a = 0; a < 3; ++a) tb[12 + a] += vcob[a];
+                            tb[15] += r[1] * vcob[2] - r[2] * vcob[1];
+                            tb[16] += r[2] * vcob[0] - r[0] * vcob[2];
+                            tb[17] += r[0] * vcob[1] - r[1] * vcob[0];
+                            rb[0] = vcob[1] * tl->w[2] - vcob[2] * tl->w[1];
+                            rb[1] = vcob[2] * tl->w[0] - vcob[0] * tl->w[2];
+                            rb[2] = vcob[0] * tl->w[1] - vcob[1] * tl->w[0];
+                            for (int a = 0; a < 3; ++a) tb[9 + a] -= rb[a];
+                            /* nw = R nref(x_ref), x_ref = R^T (x - T) */
+                            double nrb[3], Jn[9], xrb[3];
+                            for (int a = 0; a < 3; ++a)
+                                for (int c = 0; c < 3; ++c) tb[3 * a + c] += nwb[a] * nref[c];
+                            for (int c = 0; c < 3; ++c) {
+                                nrb[c] = 0.0;
+                                for (int a = 0; a < 3; ++a) nrb[c] += tl->R[3 * a + c] * nwb[a];
+                            }
+                            if (tl->kind != 2) sdf_normal_jacobian(tl->kind, tl->dims, xref_best, Jn);
+                            else for (int a = 0; a < 9; ++a) Jn[a] = 0.0;
+                            for (int c = 0; c < 3; ++c) {
+                                xrb[c] = 0.0;
+                                for (int a = 0; a < 3; ++a) xrb[c] += Jn[3 * a + c] * nrb[a];
+                            }
+                            for (int c = 0; c < 3; ++c)
+                                for (int a = 0; a < 3; ++a) tb[3 * c + a] += r[c] * xrb[a];
+                            for (int c = 0; c < 3; ++c) {
+                                double s = 0.0;
+                                for (int a = 0; a < 3; ++a) s += tl->R[3 * c + a] * xrb[a];
+                                tb[9 + c] -= s;
+                            }
+                            for (int a = 0; a < 3; ++a) vbar[a] = vrelb[a];
+                        }
+                    }
+                }
+                /* v = mv / m + dt g */
+                double dotv = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    gmvb[3 * I + a] = vbar[a] / gm[I];
+                    dotv += vbar[a] * gmv[3 * I + a];
+                }
+                gmb[I] = -dotv / (gm[I] * gm[I]);
+            }
+
+    /* ---- P2G (Eqs. 1-3, 5-6) backwards */
+    for (int64_t q = 0; q < N; ++q) {
+        const double *xp = x + 3 * q, *vp = v + 3 * q, *Cp = C + 9 * q, *Fp = F + 9 * q;
+        int base[3];
+        double fx[3], w[3][3], dw[3][3];
+        stencil_base(p, xp, base, fx);
+        for (int d = 0; d < 3; ++d) { orc_weights(fx[d], w[d]); weights_d(fx[d], dw[d]); }
+        double tau[9], A[9];
+        orc_piola_FT(mu, lam, Fp, tau);
+        for (int a = 0; a < 9; ++a) A[a] = mp * Cp[a] - dt * K * p->V0 * tau[a];
+        double Ab[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, vbp[3] = {0, 0, 0}, xbp[3] = {0, 0, 0};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    const double wip = w[0][i] * w[1][j] * w[2][k];
+                    const double gw[3] = {dw[0][i] * w[1][j] * w[2][k] * n, w[0][i] * dw[1][j] * w[2][k] * n,
+                                          w[0][i] * w[1][j] * dw[2][k] * n};
+                    const double dpos[3] = {(i - fx[0]) * dx, (j - fx[1]) * dx, (k - fx[2]) * dx};
+                    const int64_t I = node_index(n, base[0] + i, base[1] + j, base[2] + k);
+                    const double *mvb = gmvb + 3 * I;
+                    double s = gmb[I] * mp;
+                    for (int a = 0; a < 3; ++a) {
+                        double mom = mp * vp[a];
+                        for (int b = 0; b < 3; ++b) {
+                            mom += A[3 * a + b] * dpos[b];
+                            Ab[3 * a + b] += wip * mvb[a] * dpos[b];
+                        }
+                        s += mvb[a] * mom;
+                        vbp[a] += mp * wip * mvb[a];
+                    }
+                    for (int d = 0; d < 3; ++d) xbp[d] += gw[d] * s;
+                    for (int b = 0; b < 3; ++b) {
+                        double am = 0.0;
+                        for (int a = 0; a < 3; ++a) am += A[3 * a + b] * mvb[a];
+                        xbp[b] -= wip * am;
+                    }
+                }
+        /* A = m C - dt (4/dx^2) V0 tau,  tau = mu (F F^T - I) + lam ln(J) I */
+        double taub[9], trb = 0.0;
+        for (int a = 0; a < 9; ++a) { Cb[9 * q + a] = mp * Ab[a]; taub[a] = -dt * K * p->V0 * Ab[a]; }
+        trb = taub[0] + taub[4] + taub[8];
+        const double J = mat_det(Fp);
+        double FFt[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0.0;
+                for (int c = 0; c < 3; ++c) s += Fp[3 * a + c] * Fp[3 * b + c];
+                FFt[3 * a + b] = s - (a == b ? 1.0 : 0.0);
+            }
+        double mub = 0.0;
+        for (int a = 0; a < 9; ++a) mub += taub[a] * FFt[a];
+        lame_bar[0] += mub;
+        lame_bar[1] += trb * (J > 0.0 ? log(J) : log(1e-6));
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                double s = 0.0;
+                for (int c = 0; c < 3; ++c) s += (taub[3 * a + c] + taub[3 * c + a]) * Fp[3 * c + b];
+                Fb[9 * q + 3 * a + b] += mu * s;
+            }
+        if (J > 0.0) {
+            double FiT[9];
+            mat_inv_transpose(Fp, J, FiT);
+            for (int a = 0; a < 9; ++a) Fb[9 * q + a] += lam * trb * FiT[a];
+        }
+        for (int a = 0; a < 3; ++a) { vb[3 * q + a] = vbp[a]; xb[3 * q + a] += xbp[a]; }
+    }
+    free(gm); free(gmv); free(gv); free(gvb); free(gmb); free(gmvb);
+    return 0;
+}

@@ -93,6 +93,10 @@ def lib():
             L.orc_run.argtypes = [P, TF, ct.c_int32, ct.c_int32, ct.c_int64, _D, _D, _D, _D, CN]
             L.orc_block_keys.argtypes = [ct.c_int32, ct.c_int64, ct.POINTER(ct.c_float),
                                          ct.POINTER(ct.c_uint32)]
+            L.orc_step_adjoint.argtypes = [P, TF, ct.c_int32, ct.c_int64, _D, _D, _D, _D, _D, _D, _D, _D,
+                                           _D, _D]
+            L.orc_step_adjoint.restype = ct.c_int
+            L.orc_lame_vjp.argtypes = [ct.c_double, ct.c_double, ct.c_double, ct.c_double, _D, _D]
             _lib = L
     return _lib
 
@@ -346,3 +350,127 @@ def sorted_order(keys: np.ndarray, previous: Optional[np.ndarray] = None) -> np.
     previous = np.asarray(previous, dtype=np.int64)
     idx = np.argsort(keys[previous], kind="stable")
     return previous[idx]
+
+
+# ------------------------------------------------------------- the adjoint
+
+def step_adjoint(prm: OracleParams, st: State, frames, ntools, bar):
+    """Reverse mode of one sub-step from state st (unchanged).  bar: dict of
+    the adjoints of the state after the sub-step (x, v, C, F; missing keys are
+    zero).  Returns (adjoint of the state before it, [dL/dmu, dL/dlam],
+    dL/d(frame entries) as (ntools, 18): R row-major, T, u, w)."""
+    n = st.n
+    out = {k: (np.zeros((n, c)) if bar.get(k) is None else _f64(bar[k], (n, c)).copy())
+           for k, c in (("x", 3), ("v", 3), ("C", 9), ("F", 9))}
+    lame = np.zeros(2)
+    tb = np.zeros((max(ntools, 1), 18))
+    if frames is None or ntools == 0:
+        frames = (ToolFrame * 1)()
+        ntools = 0
+    rc = lib().orc_step_adjoint(ct.byref(prm.c()), frames, int(ntools), n, _dp(st.x), _dp(st.v), _dp(st.C),
+                                _dp(st.F), _dp(out["x"]), _dp(out["v"]), _dp(out["C"]), _dp(out["F"]),
+                                _dp(lame), _dp(tb))
+    if rc != 0:
+        raise MemoryError("orc_step_adjoint: out of memory")
+    return out, lame, tb[:ntools]
+
+
+def lame_vjp(E, nu, mu_bar, lam_bar):
+    Eb = ct.c_double()
+    nb = ct.c_double()
+    lib().orc_lame_vjp(float(E), float(nu), float(mu_bar), float(lam_bar), ct.byref(Eb), ct.byref(nb))
+    return Eb.value, nb.value
+
+
+def _frame_vector(fr) -> np.ndarray:
+    return np.array(list(fr.R) + list(fr.T) + list(fr.u) + list(fr.w))
+
+
+def frame_jacobian(shape, pose0, pose1, dt, field=None, h=1e-6):
+    """d(frame entries: R, T, u, w) / d(pose0, pose1) of a one-sub-step call
+    (18 x 12), by central differences of orc_tool_frames -- the map is
+    smooth (Rodrigues and its inverse away from a half turn)."""
+    p = np.concatenate([_f64(pose0, (6,)), _f64(pose1, (6,))])
+    J = np.zeros((18, 12))
+    for c in range(12):
+        a, b = p.copy(), p.copy()
+        a[c] += h
+        b[c] -= h
+        fa = _frame_vector(tool_frames(shape, a[:6], a[6:], 1, dt, field)[0])
+        fb = _frame_vector(tool_frames(shape, b[:6], b[6:], 1, dt, field)[0])
+        J[:, c] = (fa - fb) / (2 * h)
+    return J
+
+
+def rollout_frames(tools, pose_init, poses, dt):
+    """Frames of a rollout that moves tool t from pose_init[t] through
+    poses[k, t] (the pose at the end of sub-step k), one sub-step per pose."""
+    K, nt = poses.shape[0], len(tools)
+    out = (ToolFrame * max(1, K * nt))()
+    out._keep = []
+    for k in range(K):
+        for t, tool in enumerate(tools):
+            p0 = pose_init[t] if k == 0 else poses[k - 1, t]
+            fr = tool_frames(tool.shape, p0, poses[k, t], 1, dt, getattr(tool, "field", None))
+            out._keep.append(getattr(fr, "_keep", None))
+            ct.memmove(ct.byref(out, (k * nt + t) * ct.sizeof(ToolFrame)), ct.byref(fr, 0), ct.sizeof(ToolFrame))
+    return out, nt
+
+
+def rollout_loss_and_gradients(prm: OracleParams, st0: State, tools, pose_init, poses, target,
+                               checkpoint=50, final_bar=None):
+    """A rollout of K = len(poses) sub-steps from st0 (unchanged) and the
+    gradients of L = mean_p |x_p(K) - target_p|^2 (or of the loss whose
+    final-state adjoint final_bar(state) returns) with respect to E, nu, the
+    poses (K, ntools, 6) and the initial state.  Forward states are kept at
+    every `checkpoint`-th sub-step and recomputed per segment."""
+    poses = np.asarray(poses, dtype=np.float64)
+    K = poses.shape[0]
+    frames, nt = rollout_frames(tools, pose_init, poses, prm.dt)
+    fsz = ct.sizeof(ToolFrame)
+
+    def frames_at(k):
+        arr = (ToolFrame * max(1, nt))()
+        if nt:
+            ct.memmove(arr, ct.byref(frames, k * nt * fsz), nt * fsz)
+        return arr
+
+    cps = {}
+    st = st0.copy()
+    for k in range(K):
+        if k % checkpoint == 0:
+            cps[k] = st.copy()
+        run(prm, st, 1, frames_at(k), nt)
+    final = st
+    if final_bar is None:
+        diff = final.x - _f64(target, final.x.shape)
+        loss = float(np.mean(np.sum(diff * diff, axis=1)))
+        bar = {"x": 2.0 * diff / final.n}
+    else:
+        loss, bar = final_bar(final)
+    lame = np.zeros(2)
+    fbar = np.zeros((K, nt, 18))
+    for c0 in sorted(cps, reverse=True):
+        seg = [cps[c0].copy()]
+        for k in range(c0, min(c0 + checkpoint, K) - 1):
+            s = seg[-1].copy()
+            run(prm, s, 1, frames_at(k), nt)
+            seg.append(s)
+        for j in range(len(seg) - 1, -1, -1):
+            k = c0 + j
+            bar, lb, tb = step_adjoint(prm, seg[j], frames_at(k), nt, bar)
+            lame += lb
+            if nt:
+                fbar[k] = tb
+    Eb, nub = lame_vjp(prm.E, prm.nu, lame[0], lame[1])
+    pose_bar = np.zeros_like(poses)
+    for k in range(K):
+        for t, tool in enumerate(tools):
+            p0 = pose_init[t] if k == 0 else poses[k - 1, t]
+            J = frame_jacobian(tool.shape, p0, poses[k, t], prm.dt, getattr(tool, "field", None))
+            g = J.T @ fbar[k, t]
+            pose_bar[k, t] += g[6:]
+            if k > 0:
+                pose_bar[k - 1, t] += g[:6]
+    return {"loss": loss, "E": Eb, "nu": nub, "poses": pose_bar, "state0": bar, "final": final,
+            "lame": lame, "frames": fbar}

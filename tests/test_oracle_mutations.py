@@ -1,7 +1,7 @@
 """The oracle's pins have teeth: plant a plausible mistake in a copy of the
 oracle source (a dropped term, a wrong sign, a transposed operand, a wrong
-index, the garbled printed form of Eq. 5), build it, and check that the pin
-suite fails on it.  Runs on the CPU only; the real oracle is untouched."""
+index, the garbled printed form of Eq. 5; in the forward step and in its
+adjoint), build it, and check that the pin suites fail on it.  Runs on the CPU only; the real oracle is untouched."""
 import os
 import subprocess
 import sys
@@ -41,6 +41,19 @@ MUTATIONS = {
     "sampled faces not one-sided": ("const double span = (double)(hi[a] - lo[a]) * h;", "const double span = 2.0 * h;"),
     "sampled outside counts as contact": ("            return INFINITY;\n        }\n        c[a] = (int64_t)f;",
                                           "            return -1.0;\n        }\n        c[a] = (int64_t)f;"),
+    "adjoint drops dt x_bar": ("vbt[a] = vbo[a] + dt * xbo[a];", "vbt[a] = vbo[a];"),
+    "adjoint F update transposed": ("sF += IdtC[3 * c + a] * Fbo[3 * c + b];", "sF += IdtC[3 * a + c] * Fbo[3 * c + b];"),
+    "adjoint C from F product transposed": ("sC += Fbo[3 * a + c] * Fp[3 * b + c];", "sC += Fbo[3 * a + c] * Fp[3 * c + b];"),
+    "adjoint weight slope sign": ("    dw[0] = -(1.5 - fx);", "    dw[0] = (1.5 - fx);"),
+    "adjoint grid mass sign": ("gmb[I] = -dotv / (gm[I] * gm[I]);", "gmb[I] = dotv / (gm[I] * gm[I]);"),
+    "adjoint friction slope dropped": ("vnb += p->friction * scb / vtn;", "vnb += 0.0;"),
+    "adjoint tool spin dropped": ("tb[15] += r[1] * vcob[2] - r[2] * vcob[1];", "tb[15] += 0.0;"),
+    "adjoint normal curvature dropped": ("if (tl->kind != 2) sdf_normal_jacobian(tl->kind, tl->dims, xref_best, Jn);",
+                                         "if (0) sdf_normal_jacobian(tl->kind, tl->dims, xref_best, Jn);"),
+    "adjoint stress uses tau not its symmetrisation": ("s += (taub[3 * a + c] + taub[3 * c + a]) * Fp[3 * c + b];",
+                                                       "s += 2.0 * taub[3 * a + c] * Fp[3 * c + b];"),
+    "adjoint lambda uses J": ("lame_bar[1] += trb * (J > 0.0 ? log(J) : log(1e-6));", "lame_bar[1] += trb * J;"),
+    "adjoint dpos term dropped in P2G": ("xbp[b] -= wip * am;", "xbp[b] -= 0.0 * am;"),
     "block key axis order": ("keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));", "keys[q] = (uint32_t)(b[2] + nb * (b[1] + nb * b[0]));"),
 }
 
@@ -57,6 +70,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                            "-o", str(lib), str(mutated), "-lm"])
     env = dict(os.environ, ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_adjoint_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "planted mistake '%s' passed every pin" % name
