@@ -392,6 +392,97 @@ double orc_sdf_sampled(const float *sdf, int32_t res, const double *o, double h,
 
 /* ------------------------------------------- grid operation (Eq. 7, 11-19) */
 
+/* What the contact response of one node computed (Eqs. 15-19), kept for the
+ * margins and for the adjoint. */
+typedef struct {
+    double nw[3];         /* world unit normal R nref */
+    double r[3];          /* x - T */
+    double vco[3];        /* rigid tool velocity at the node */
+    double vrel[3];       /* Eq. 15 */
+    double vn;            /* Eq. 16 */
+    double vt[3];         /* Eq. 17 */
+    double vtn;           /* |v_t| */
+    double s;             /* |v_t| + mu_f v_n, the unclamped Eq. 18 length */
+    double scale;         /* clamped Eq. 18 factor on v_t */
+    int projected;        /* v_n < 0: Eqs. 17-19 applied */
+} orc_contact;
+
+/* z-buffer of Sec. III-C at the world node position xw: the tool with the
+ * smallest distance (lowest index on ties).  Returns that distance (+inf if
+ * no tool); *id, nref and xref receive the tool, its reference-frame normal
+ * and the node's reference-frame position; *d2 the second-smallest distance;
+ * *cells (if given) the smallest sample-cell margin of a sampled field whose
+ * sample lies within 2h of theta. */
+static double nearest_tool(const orc_tool *tools, int32_t ntools, double theta, const double *xw,
+                           int *id, double *nref, double *xref, double *d2, double *cells)
+{
+    double dmin = INFINITY;
+    *id = -1;
+    *d2 = INFINITY;
+    if (cells) *cells = INFINITY;
+    for (int t = 0; t < ntools; ++t) {
+        const orc_tool *tl = tools + t;
+        double xr[3], nr[3];
+        for (int a = 0; a < 3; ++a) {   /* Eq. 11: R^-1 (x - T) */
+            double s = 0.0;
+            for (int b = 0; b < 3; ++b) s += tl->R[3 * b + a] * (xw[b] - tl->T[b]);
+            xr[a] = s;
+        }
+        double cm = INFINITY;
+        const double d = tl->kind == 2 ? orc_sdf_sampled(tl->sdf, tl->res, tl->dims, tl->h, xr, nr, &cm)
+                                       : orc_sdf(tl->kind, tl->dims, xr, nr);
+        /* a neighbouring sample of a distance field differs by at most
+           sqrt(3) h, so the cell decision matters only near contact */
+        if (cells && d < theta + 2.0 * tl->h && cm < *cells) *cells = cm;
+        if (d < dmin) {
+            *d2 = dmin;
+            dmin = d; *id = t;
+            for (int a = 0; a < 3; ++a) { nref[a] = nr[a]; xref[a] = xr[a]; }
+        } else if (d < *d2) {
+            *d2 = d;
+        }
+    }
+    return dmin;
+}
+
+/* Eqs. 15-19 at a node at xw in contact with tool tl whose reference-frame
+ * normal is nref: v is replaced by the response (unchanged if separating). */
+static void contact_response(const orc_params *p, const orc_tool *tl, const double *xw, const double *nref,
+                             double *v, orc_contact *c)
+{
+    for (int a = 0; a < 3; ++a) {
+        c->nw[a] = 0.0;
+        for (int b = 0; b < 3; ++b) c->nw[a] += tl->R[3 * a + b] * nref[b];
+        c->r[a] = xw[a] - tl->T[a];
+    }
+    c->vco[0] = tl->u[0] + tl->w[1] * c->r[2] - tl->w[2] * c->r[1];
+    c->vco[1] = tl->u[1] + tl->w[2] * c->r[0] - tl->w[0] * c->r[2];
+    c->vco[2] = tl->u[2] + tl->w[0] * c->r[1] - tl->w[1] * c->r[0];
+    c->vn = 0.0;
+    for (int a = 0; a < 3; ++a) { c->vrel[a] = v[a] - c->vco[a]; c->vn += c->vrel[a] * c->nw[a]; }  /* Eq. 15-16 */
+    c->projected = 0;
+    c->vtn = 0.0;
+    c->s = 0.0;
+    c->scale = 1.0;
+    if (c->vn < 0.0) {
+        c->projected = 1;
+        for (int a = 0; a < 3; ++a) { c->vt[a] = c->vrel[a] - c->vn * c->nw[a]; c->vtn += c->vt[a] * c->vt[a]; }  /* Eq. 17 */
+        c->vtn = sqrt(c->vtn);
+        c->scale = 0.0;             /* Eq. 18, clamped */
+        if (c->vtn > 0.0) {
+            c->s = c->vtn + p->friction * c->vn;
+            c->scale = c->s > 0.0 ? c->s / c->vtn : 0.0;
+        }
+        for (int a = 0; a < 3; ++a) v[a] = c->scale * c->vt[a] + c->vco[a];  /* Eq. 19 */
+    }
+}
+
+static inline int in_wall_band(const orc_params *p, int i, int j, int k)
+{
+    const int b = p->bound, n = p->n_grid;
+    return i < b || j < b || k < b || i >= n - b || j >= n - b || k >= n - b;
+}
+
 /* grid_v: n^3 x 3 output.  contact (optional, n^3): index of the tool whose
  * projection was applied, -1 otherwise.  margin (optional, n^3): distance of
  * this node's floating-point decisions from a branch point -- min over
@@ -416,64 +507,21 @@ void orc_grid_update(const orc_params *p, const orc_tool *tools, int32_t ntools,
                         v[a] = grid_mv[3 * I + a] / grid_m[I] + p->dt * p->gravity[a];  /* Eq. 7 + gravity */
                     if (ntools > 0) {
                         const double xw[3] = {i * dx, j * dx, k * dx};
-                        double dmin = INFINITY, d2 = INFINITY, nref_best[3] = {0, 0, 0}, cells = INFINITY;
-                        int id = -1;
-                        for (int t = 0; t < ntools; ++t) {
-                            const orc_tool *tl = tools + t;
-                            double xr[3], nr[3];
-                            for (int a = 0; a < 3; ++a) {   /* Eq. 11: R^-1 (x - T) */
-                                double s = 0.0;
-                                for (int b = 0; b < 3; ++b) s += tl->R[3 * b + a] * (xw[b] - tl->T[b]);
-                                xr[a] = s;
-                            }
-                            double cm = INFINITY;
-                            const double d = tl->kind == 2 ? orc_sdf_sampled(tl->sdf, tl->res, tl->dims, tl->h, xr, nr, &cm)
-                                                           : orc_sdf(tl->kind, tl->dims, xr, nr);
-                            /* a neighbouring sample of a distance field differs by at most
-                               sqrt(3) h, so the cell decision matters only near contact */
-                            if (d < p->theta + 2.0 * tl->h && cm < cells) cells = cm;
-                            if (d < dmin) {
-                                d2 = dmin;
-                                dmin = d; id = t;
-                                nref_best[0] = nr[0]; nref_best[1] = nr[1]; nref_best[2] = nr[2];
-                            } else if (d < d2) {
-                                d2 = d;
-                            }
-                        }
+                        double nref[3], xref[3], d2, cells;
+                        int id;
+                        const double dmin = nearest_tool(tools, ntools, p->theta, xw, &id, nref, xref, &d2, &cells);
                         mg = dmin < INFINITY ? fabs(dmin - p->theta) : INFINITY;
                         if (d2 < INFINITY && d2 - dmin < mg) mg = d2 - dmin;
                         if (cells < mg) mg = cells;
                         if (dmin < p->theta) {
-                            const orc_tool *tl = tools + id;
-                            double nw[3], r[3], vco[3], vrel[3];
-                            for (int a = 0; a < 3; ++a) {
-                                nw[a] = 0.0;
-                                for (int b = 0; b < 3; ++b) nw[a] += tl->R[3 * a + b] * nref_best[b];
-                                r[a] = xw[a] - tl->T[a];
-                            }
-                            vco[0] = tl->u[0] + tl->w[1] * r[2] - tl->w[2] * r[1];
-                            vco[1] = tl->u[1] + tl->w[2] * r[0] - tl->w[0] * r[2];
-                            vco[2] = tl->u[2] + tl->w[0] * r[1] - tl->w[1] * r[0];
-                            double vn = 0.0;
-                            for (int a = 0; a < 3; ++a) { vrel[a] = v[a] - vco[a]; vn += vrel[a] * nw[a]; }  /* Eq. 15-16 */
-                            if (fabs(vn) < mg) mg = fabs(vn);
-                            if (vn < 0.0) {
-                                double vt[3], vtn = 0.0;
-                                for (int a = 0; a < 3; ++a) { vt[a] = vrel[a] - vn * nw[a]; vtn += vt[a] * vt[a]; }  /* Eq. 17 */
-                                vtn = sqrt(vtn);
-                                double scale = 0.0;             /* Eq. 18, clamped */
-                                if (vtn > 0.0) {
-                                    const double s = vtn + p->friction * vn;
-                                    scale = s > 0.0 ? s / vtn : 0.0;
-                                    if (fabs(s) < mg) mg = fabs(s);
-                                }
-                                for (int a = 0; a < 3; ++a) v[a] = scale * vt[a] + vco[a];  /* Eq. 19 */
-                            }
+                            orc_contact c;
+                            contact_response(p, tools + id, xw, nref, v, &c);
+                            if (fabs(c.vn) < mg) mg = fabs(c.vn);
+                            if (c.projected && c.vtn > 0.0 && fabs(c.s) < mg) mg = fabs(c.s);
                             hit = id;
                         }
                     }
-                    const int b = p->bound;
-                    if (i < b || j < b || k < b || i >= n - b || j >= n - b || k >= n - b) {
+                    if (in_wall_band(p, i, j, k)) {
                         v[0] = v[1] = v[2] = 0.0;          /* sticky walls */
                         mg = INFINITY;
                         hit = -1;
@@ -733,8 +781,7 @@ int orc_step_adjoint(const orc_params *p, const orc_tool *tools, int32_t ntools,
             for (int k = 0; k < n; ++k) {
                 const int64_t I = node_index(n, i, j, k);
                 if (!(gm[I] > 0.0)) continue;                      /* v = 0: no dependence */
-                const int b = p->bound;
-                if (i < b || j < b || k < b || i >= n - b || j >= n - b || k >= n - b) continue;
+                if (in_wall_band(p, i, j, k)) continue;
                 double vf[3], vbar[3];
                 for (int a = 0; a < 3; ++a) {
                     vf[a] = gmv[3 * I + a] / gm[I] + dt * p->gravity[a];
@@ -742,69 +789,40 @@ int orc_step_adjoint(const orc_params *p, const orc_tool *tools, int32_t ntools,
                 }
                 if (ntools > 0) {
                     const double xw[3] = {i * dx, j * dx, k * dx};
-                    double dmin = INFINITY, nref[3] = {0, 0, 0}, xref_best[3] = {0, 0, 0};
-                    int id = -1;
-                    for (int t = 0; t < ntools; ++t) {
-                        const orc_tool *tl = tools + t;
-                        double xr[3], nr[3];
-                        for (int a = 0; a < 3; ++a) {
-                            double s = 0.0;
-                            for (int c = 0; c < 3; ++c) s += tl->R[3 * c + a] * (xw[c] - tl->T[c]);
-                            xr[a] = s;
-                        }
-                        const double d = tl->kind == 2 ? orc_sdf_sampled(tl->sdf, tl->res, tl->dims, tl->h, xr, nr, NULL)
-                                                       : orc_sdf(tl->kind, tl->dims, xr, nr);
-                        if (d < dmin) {
-                            dmin = d; id = t;
-                            for (int a = 0; a < 3; ++a) { nref[a] = nr[a]; xref_best[a] = xr[a]; }
-                        }
-                    }
+                    double nref[3], xref[3], d2;
+                    int id;
+                    const double dmin = nearest_tool(tools, ntools, p->theta, xw, &id, nref, xref, &d2, NULL);
                     if (dmin < p->theta) {
                         const orc_tool *tl = tools + id;
-                        double nw[3], r[3], vco[3], vrel[3], vn = 0.0;
-                        for (int a = 0; a < 3; ++a) {
-                            nw[a] = 0.0;
-                            for (int c = 0; c < 3; ++c) nw[a] += tl->R[3 * a + c] * nref[c];
-                            r[a] = xw[a] - tl->T[a];
-                        }
-                        vco[0] = tl->u[0] + tl->w[1] * r[2] - tl->w[2] * r[1];
-                        vco[1] = tl->u[1] + tl->w[2] * r[0] - tl->w[0] * r[2];
-                        vco[2] = tl->u[2] + tl->w[0] * r[1] - tl->w[1] * r[0];
-                        for (int a = 0; a < 3; ++a) { vrel[a] = vf[a] - vco[a]; vn += vrel[a] * nw[a]; }
-                        if (vn < 0.0) {
-                            double vt[3], vtn = 0.0;
-                            for (int a = 0; a < 3; ++a) { vt[a] = vrel[a] - vn * nw[a]; vtn += vt[a] * vt[a]; }
-                            vtn = sqrt(vtn);
-                            double scale = 0.0;
-                            if (vtn > 0.0) {
-                                const double s = vtn + p->friction * vn;
-                                scale = s > 0.0 ? s / vtn : 0.0;
-                            }
+                        double vout[3] = {vf[0], vf[1], vf[2]};
+                        orc_contact c;
+                        contact_response(p, tl, xw, nref, vout, &c);
+                        if (c.projected) {
                             /* v' = scale vt + vco */
                             double vtb[3] = {0, 0, 0}, vnb = 0.0, nwb[3], vrelb[3], vcob[3];
-                            if (scale > 0.0) {
+                            if (c.scale > 0.0) {
                                 double scb = 0.0;
-                                for (int a = 0; a < 3; ++a) { vtb[a] = scale * vbar[a]; scb += vbar[a] * vt[a]; }
+                                for (int a = 0; a < 3; ++a) { vtb[a] = c.scale * vbar[a]; scb += vbar[a] * c.vt[a]; }
                                 /* scale = 1 + mu_f vn / |vt| */
-                                vnb += p->friction * scb / vtn;
-                                const double vtnb = -p->friction * vn * scb / (vtn * vtn);
-                                for (int a = 0; a < 3; ++a) vtb[a] += vtnb * vt[a] / vtn;
+                                vnb += p->friction * scb / c.vtn;
+                                const double vtnb = -p->friction * c.vn * scb / (c.vtn * c.vtn);
+                                for (int a = 0; a < 3; ++a) vtb[a] += vtnb * c.vt[a] / c.vtn;
                             }
                             /* vt = vrel - vn nw */
                             double vtb_n = 0.0;
-                            for (int a = 0; a < 3; ++a) { vrelb[a] = vtb[a]; vtb_n += vtb[a] * nw[a]; nwb[a] = -vn * vtb[a]; }
+                            for (int a = 0; a < 3; ++a) { vrelb[a] = vtb[a]; vtb_n += vtb[a] * c.nw[a]; nwb[a] = -c.vn * vtb[a]; }
                             vnb -= vtb_n;
                             /* vn = vrel . nw */
-                            for (int a = 0; a < 3; ++a) { vrelb[a] += vnb * nw[a]; nwb[a] += vnb * vrel[a]; }
+                            for (int a = 0; a < 3; ++a) { vrelb[a] += vnb * c.nw[a]; nwb[a] += vnb * c.vrel[a]; }
                             /* vrel = v - vco, and v' carries + vco */
                             for (int a = 0; a < 3; ++a) vcob[a] = vbar[a] - vrelb[a];
                             double *tb = tool_bar + 18 * id;           /* R[9], T[3], u[3], w[3] */
                             /* vco = u + w x r, r = x - T */
                             double rb[3];
                             for (int a = 0; a < 3; ++a) tb[12 + a] += vcob[a];
-                            tb[15] += r[1] * vcob[2] - r[2] * vcob[1];
-                            tb[16] += r[2] * vcob[0] - r[0] * vcob[2];
-                            tb[17] += r[0] * vcob[1] - r[1] * vcob[0];
+                            tb[15] += c.r[1] * vcob[2] - c.r[2] * vcob[1];
+                            tb[16] += c.r[2] * vcob[0] - c.r[0] * vcob[2];
+                            tb[17] += c.r[0] * vcob[1] - c.r[1] * vcob[0];
                             rb[0] = vcob[1] * tl->w[2] - vcob[2] * tl->w[1];
                             rb[1] = vcob[2] * tl->w[0] - vcob[0] * tl->w[2];
                             rb[2] = vcob[0] * tl->w[1] - vcob[1] * tl->w[0];
@@ -812,23 +830,23 @@ int orc_step_adjoint(const orc_params *p, const orc_tool *tools, int32_t ntools,
                             /* nw = R nref(x_ref), x_ref = R^T (x - T) */
                             double nrb[3], Jn[9], xrb[3];
                             for (int a = 0; a < 3; ++a)
-                                for (int c = 0; c < 3; ++c) tb[3 * a + c] += nwb[a] * nref[c];
-                            for (int c = 0; c < 3; ++c) {
-                                nrb[c] = 0.0;
-                                for (int a = 0; a < 3; ++a) nrb[c] += tl->R[3 * a + c] * nwb[a];
+                                for (int e = 0; e < 3; ++e) tb[3 * a + e] += nwb[a] * nref[e];
+                            for (int e = 0; e < 3; ++e) {
+                                nrb[e] = 0.0;
+                                for (int a = 0; a < 3; ++a) nrb[e] += tl->R[3 * a + e] * nwb[a];
                             }
-                            if (tl->kind != 2) sdf_normal_jacobian(tl->kind, tl->dims, xref_best, Jn);
+                            if (tl->kind != 2) sdf_normal_jacobian(tl->kind, tl->dims, xref, Jn);
                             else for (int a = 0; a < 9; ++a) Jn[a] = 0.0;
-                            for (int c = 0; c < 3; ++c) {
-                                xrb[c] = 0.0;
-                                for (int a = 0; a < 3; ++a) xrb[c] += Jn[3 * a + c] * nrb[a];
+                            for (int e = 0; e < 3; ++e) {
+                                xrb[e] = 0.0;
+                                for (int a = 0; a < 3; ++a) xrb[e] += Jn[3 * a + e] * nrb[a];
                             }
-                            for (int c = 0; c < 3; ++c)
-                                for (int a = 0; a < 3; ++a) tb[3 * c + a] += r[c] * xrb[a];
-                            for (int c = 0; c < 3; ++c) {
+                            for (int e = 0; e < 3; ++e)
+                                for (int a = 0; a < 3; ++a) tb[3 * e + a] += c.r[e] * xrb[a];
+                            for (int e = 0; e < 3; ++e) {
                                 double s = 0.0;
-                                for (int a = 0; a < 3; ++a) s += tl->R[3 * c + a] * xrb[a];
-                                tb[9 + c] -= s;
+                                for (int a = 0; a < 3; ++a) s += tl->R[3 * e + a] * xrb[a];
+                                tb[9 + e] -= s;
                             }
                             for (int a = 0; a < 3; ++a) vbar[a] = vrelb[a];
                         }

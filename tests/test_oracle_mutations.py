@@ -25,10 +25,10 @@ MUTATIONS = {
     "advect with old v": ("vp[a] = vnew[a];\n            xp[a] += p->dt * vnew[a];",
                           "xp[a] += p->dt * vp[a];\n            vp[a] = vnew[a];"),
     "x_ref uses R not R^T": ("s += tl->R[3 * b + a] * (xw[b] - tl->T[b]);", "s += tl->R[3 * a + b] * (xw[b] - tl->T[b]);"),
-    "friction not clamped": ("scale = s > 0.0 ? s / vtn : 0.0;", "scale = s / vtn;"),
-    "projects separating nodes": ("if (vn < 0.0) {", "if (vn < 1e30) {"),
-    "normal not rotated": ("nw[a] += tl->R[3 * a + b] * nref_best[b];", "nw[a] += tl->R[3 * b + a] * nref_best[b];"),
-    "tool velocity drops spin": ("vco[0] = tl->u[0] + tl->w[1] * r[2] - tl->w[2] * r[1];", "vco[0] = tl->u[0];"),
+    "friction not clamped": ("c->scale = c->s > 0.0 ? c->s / c->vtn : 0.0;", "c->scale = c->s / c->vtn;"),
+    "projects separating nodes": ("if (c->vn < 0.0) {", "if (c->vn < 1e30) {"),
+    "normal not rotated": ("c->nw[a] += tl->R[3 * a + b] * nref[b];", "c->nw[a] += tl->R[3 * b + a] * nref[b];"),
+    "tool velocity drops spin": ("c->vco[0] = tl->u[0] + tl->w[1] * c->r[2] - tl->w[2] * c->r[1];", "c->vco[0] = tl->u[0];"),
     "z-buffer picks farthest": ("if (d < dmin) {", "if (d > dmin || dmin == INFINITY) {"),
     "walls ignored": ("v[0] = v[1] = v[2] = 0.0;          /* sticky walls */", ";"),
     "sampled index rounds": ("const double f = floor(u);", "const double f = floor(u + 0.5);"),
@@ -46,10 +46,10 @@ MUTATIONS = {
     "adjoint C from F product transposed": ("sC += Fbo[3 * a + c] * Fp[3 * b + c];", "sC += Fbo[3 * a + c] * Fp[3 * c + b];"),
     "adjoint weight slope sign": ("    dw[0] = -(1.5 - fx);", "    dw[0] = (1.5 - fx);"),
     "adjoint grid mass sign": ("gmb[I] = -dotv / (gm[I] * gm[I]);", "gmb[I] = dotv / (gm[I] * gm[I]);"),
-    "adjoint friction slope dropped": ("vnb += p->friction * scb / vtn;", "vnb += 0.0;"),
-    "adjoint tool spin dropped": ("tb[15] += r[1] * vcob[2] - r[2] * vcob[1];", "tb[15] += 0.0;"),
-    "adjoint normal curvature dropped": ("if (tl->kind != 2) sdf_normal_jacobian(tl->kind, tl->dims, xref_best, Jn);",
-                                         "if (0) sdf_normal_jacobian(tl->kind, tl->dims, xref_best, Jn);"),
+    "adjoint friction slope dropped": ("vnb += p->friction * scb / c.vtn;", "vnb += 0.0;"),
+    "adjoint tool spin dropped": ("tb[15] += c.r[1] * vcob[2] - c.r[2] * vcob[1];", "tb[15] += 0.0;"),
+    "adjoint normal curvature dropped": ("if (tl->kind != 2) sdf_normal_jacobian(tl->kind, tl->dims, xref, Jn);",
+                                         "if (0) sdf_normal_jacobian(tl->kind, tl->dims, xref, Jn);"),
     "adjoint stress uses tau not its symmetrisation": ("s += (taub[3 * a + c] + taub[3 * c + a]) * Fp[3 * c + b];",
                                                        "s += 2.0 * taub[3 * a + c] * Fp[3 * c + b];"),
     "adjoint lambda uses J": ("lame_bar[1] += trb * (J > 0.0 ? log(J) : log(1e-6));", "lame_bar[1] += trb * J;"),
