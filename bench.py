@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--substeps", type=int, default=25)
     ap.add_argument("--pipeline", default="fused", choices=["fused", "split"])
     ap.add_argument("--no-secondary", action="store_true", help="skip the 30K slab line")
+    ap.add_argument("--no-differentiable", action="store_true", help="skip the differentiable-rollout line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-environment measurement")
     ap.add_argument("--batch-envs", type=int, default=256)
@@ -293,6 +294,77 @@ def run_batched(args, rank, device, barrier, max_over_ranks, steps=6, loop_steps
             "gpu_launches_per_step": S}
 
 
+def run_differentiable(args, rank, device, barrier, max_over_ranks, reps=2):
+    """The differentiable rollout (SURVEY config 5): the 30K slab over 500
+    sub-steps with checkpoints every 50, loss = mean |x(T) - target|^2 with
+    a target rolled out on the GPU with E = 1.2e4, nu = 0.33 and shifted
+    poses.  Times the recorded forward pass (mpm_tape_record) and the reverse
+    pass (mpm_tape_backward, which recomputes every segment), against a
+    plain split-pipeline forward of the same sub-steps."""
+    import torch
+    from paper_2402_01181_gb300 import dist as D
+    from paper_2402_01181_gb300 import mpm
+    case = scenes.slab30k_diff(seed=D.replica_seed(rank))
+    sc = case.scene
+    K = case.poses.shape[0]
+    stream = torch.cuda.current_stream(device)
+
+    def fresh(E, nu, poses, record=True):
+        si = mpm.sim_from_scene(sc, pipeline=mpm.MPM_PIPELINE_SPLIT, load=False)
+        si.set_env_material(0, E, nu, sc.rho)
+        si.load(sc.x, sc.particle_volume)
+        si.set_tool(0, case.pose_init[0], sc.tools[0].shape)
+        return si
+
+    tgt = fresh(case.target_E, case.target_nu, case.target_poses)
+    tgt.tape_record(case.target_poses, case.checkpoint)
+    target = torch.tensor(tgt.read()["x"], device=device)
+    tgt.close()
+    fwd, bwd, plain = [], [], []
+    res = {}
+    for r in range(reps + 1):
+        si = fresh(sc.E, sc.nu, case.poses)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        barrier()
+        a.record(stream)
+        si.tape_record(case.poses, case.checkpoint)
+        b.record(stream)
+        x = torch.empty((sc.n, 3), dtype=torch.float32, device=device)
+        si.read_device(x=x)
+        loss = float(((x - target) ** 2).sum(dim=1).mean())
+        gx = 2.0 * (x - target) / sc.n
+        torch.cuda.synchronize(device)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        g = si.tape_backward(gx)
+        c.record(stream)
+        torch.cuda.synchronize(device)
+        si.close()
+        # the same sub-steps without the record: one mpm_step call per pose
+        sp = fresh(sc.E, sc.nu, case.poses)
+        d, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d.record(stream)
+        for k in range(K):
+            sp.set_tool(0, case.poses[k, 0], sc.tools[0].shape)
+            sp.step(1)
+        e.record(stream)
+        torch.cuda.synchronize(device)
+        sp.close()
+        if r == 0:
+            continue                      # warm-up
+        fwd.append(a.elapsed_time(b))
+        bwd.append(c0.elapsed_time(c))
+        plain.append(d.elapsed_time(e))
+        res = {"loss": loss, "dL_dE": g["E"], "dL_dnu": g["nu"],
+               "max_abs_dL_dpose": float(abs(g["poses"]).max())}
+    f, bk, pl = max_over_ranks(min(fwd)), max_over_ranks(min(bwd)), max_over_ranks(min(plain))
+    res.update({"workload": "slab30k_diff", "particles": sc.n, "substeps": K, "checkpoint_every": case.checkpoint,
+                "forward_record_ms": f, "backward_ms": bk, "plain_forward_ms": pl,
+                "backward_over_forward": bk / f, "backward_over_plain_forward": bk / pl,
+                "note": "min over %d repetitions; backward includes the segment recomputation" % reps})
+    return res
+
+
 def algorithmic_bytes_per_particle_step(n, active_nodes, S):
     """Minimum DRAM traffic of one fused sub-step, per particle: the particle
     state is read and written once (x, id: 16 B; F: 36 B; twice = 104 B); each
@@ -395,6 +467,9 @@ def main():
     batched = None
     if not args.no_batched:
         batched = run_batched(args, rank, device, barrier, max_over_ranks)
+    differentiable = None
+    if not args.no_differentiable:
+        differentiable = run_differentiable(args, rank, device, barrier, max_over_ranks)
 
     if rank != 0:
         ranks.close()
@@ -437,6 +512,7 @@ def main():
         "clocks": main_res["clocks"],
         "secondary": second,
         "batched": batched,
+        "differentiable": differentiable,
     }
     print(json.dumps(line))
     ranks.close()

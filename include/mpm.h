@@ -221,6 +221,39 @@ mpm_status mpm_grid_velocity(mpm_handle *h, float *v, int on_device);
  * Host arrays of n entries.  Synchronises. */
 mpm_status mpm_read_order(mpm_handle *h, uint32_t *ids, uint32_t *keys);
 
+/* -------------------------------------------------- differentiable rollout */
+
+/* Record a rollout of n_substeps sub-steps for mpm_tape_backward: sub-step k
+ * moves every tool from its pose at the end of sub-step k-1 (for k = 0, its
+ * current pose) to poses[(k * n_tools + t) * 6 ...] (T, rotation vector;
+ * n_tools = highest tool slot in use + 1) -- the same as calling
+ * mpm_set_tool_pose with those poses and mpm_step(1) n_substeps times.
+ * The handle's state advances to the end of the rollout.  The particle state
+ * is stored every checkpoint_every sub-steps (24 floats per particle each);
+ * mpm_tape_backward recomputes the sub-steps in between.  The paper does not
+ * differentiate its simulator (Sec. V names differentiable physics as future
+ * work); this is the plain reverse mode of the sub-step defined above.
+ * Needs a handle with MPM_PIPELINE_SPLIT and one environment (MPM_ERR_STATE
+ * otherwise).  poses: host array.  Device memory for the record is taken
+ * from the handle's allocator and kept (and reused) until mpm_destroy. */
+mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *poses,
+                           int32_t checkpoint_every);
+
+/* Reverse mode of the recorded rollout.  x_bar (n x 3), v_bar (n x 3),
+ * F_bar (n x 9), C_bar (n x 9): dL/d(final state) in load order; NULL = 0.
+ * Outputs (each may be NULL): grad_material[2] = dL/dE, dL/dnu (through
+ * Eq. 6); grad_poses = dL/dposes, laid out as mpm_tape_record's poses
+ * (host, double); x0_bar, v0_bar, F0_bar, C0_bar = dL/d(state before the
+ * rollout).  on_device applies to the float arrays (inputs and outputs);
+ * grad_material and grad_poses are host arrays.  Each branch of the forward
+ * pass (contact, approaching test, friction clamp, closest tool, walls,
+ * m > 0) is held at the side taken; distances and sampled fields give no
+ * derivative.  Material and tools must be unchanged since the record
+ * (MPM_ERR_STATE).  Synchronises. */
+mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_bar, const float *F_bar,
+                             const float *C_bar, int on_device, double *grad_material, double *grad_poses,
+                             float *x0_bar, float *v0_bar, float *F0_bar, float *C0_bar);
+
 /* ------------------------------------------------------ without allocation */
 
 /* The stable block sort that mpm_load_particles performs, for callers that

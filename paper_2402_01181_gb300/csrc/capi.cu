@@ -16,6 +16,7 @@
 #include "../../include/mpm.h"
 #include "common.cuh"
 #include "launch.h"
+#include "rotation.h"
 
 using namespace gbmpm;
 
@@ -40,39 +41,6 @@ mpm_status fail(mpm_status st, const char *fmt, ...) {
     } while (0)
 
 
-// ------------------------------------------------------------ rotations
-
-struct Quat {
-    double w, x, y, z;
-};
-Quat qmul(const Quat &a, const Quat &b) {
-    return {a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z, a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
-            a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x, a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
-}
-Quat qexp_rotvec(const double r[3]) {
-    const double th = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    if (th < 1e-12) {
-        Quat q{1.0, 0.5 * r[0], 0.5 * r[1], 0.5 * r[2]};
-        const double nq = std::sqrt(q.w * q.w + q.x * q.x + q.y * q.y + q.z * q.z);
-        return {q.w / nq, q.x / nq, q.y / nq, q.z / nq};
-    }
-    const double s = std::sin(0.5 * th) / th;
-    return {std::cos(0.5 * th), s * r[0], s * r[1], s * r[2]};
-}
-void qlog_rotvec(Quat q, double r[3]) {   // shortest rotation
-    if (q.w < 0) { q.w = -q.w; q.x = -q.x; q.y = -q.y; q.z = -q.z; }
-    const double v = std::sqrt(q.x * q.x + q.y * q.y + q.z * q.z);
-    if (v < 1e-12) { r[0] = 2 * q.x; r[1] = 2 * q.y; r[2] = 2 * q.z; return; }
-    const double th = 2.0 * std::atan2(v, q.w);
-    r[0] = th * q.x / v; r[1] = th * q.y / v; r[2] = th * q.z / v;
-}
-void qmatrix(const Quat &q, double R[9]) {
-    const double w = q.w, x = q.x, y = q.y, z = q.z;
-    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z); R[2] = 2 * (x * z + w * y);
-    R[3] = 2 * (x * y + w * z); R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
-    R[6] = 2 * (x * z - w * y); R[7] = 2 * (y * z + w * x); R[8] = 1 - 2 * (x * x + y * y);
-}
-
 struct HostTool {
     int kind = MPM_TOOL_NONE;
     int field = -1;                       // MPM_TOOL_SAMPLED: index into mpm_handle::fields
@@ -92,6 +60,28 @@ struct HostField {
     int res = 0;
     double origin[3] = {0, 0, 0};
     double h = 0;
+};
+
+// A recorded differentiable rollout (mpm_tape_record) for mpm_tape_backward.
+// A state image holds one split-pipeline particle state: xi, f0, f1, vc0,
+// vc1, vc2 (4 n floats each) then f2 (n floats, padded to a multiple of 4).
+struct Tape {
+    bool valid = false;
+    int nsub = 0, ck = 0, ntools = 0;
+    int64_t n = 0;
+    size_t image = 0;                 // floats per state image
+    size_t cap_ckpt = 0, cap_seg = 0, cap_frames = 0, cap_red = 0, cap_grid = 0, cap_abar = 0;
+    float *ckpt = nullptr;            // checkpoint images, one per ck sub-steps
+    float *seg = nullptr;             // ck images of the segment being reversed
+    float4 *seg_grid = nullptr;       // ck grids (m, mv) as the grid operation read them
+    float4 *gv = nullptr;             // grid velocities of the sub-step being reversed
+    float4 *gbar = nullptr;           // grid adjoint
+    float *abar = nullptr;            // particle adjoint: x (3n), v (3n), C (9n), F (9n)
+    ToolFrame *frames = nullptr;      // nsub x ntools (device)
+    double *red = nullptr;            // dL/dmu, dL/dlam, then nsub x ntools x 18 frame adjoints
+    std::vector<double> pose_init;    // ntools x 6
+    std::vector<double> poses;        // nsub x ntools x 6
+    double E = 0, nu = 0;
 };
 
 }  // namespace
@@ -141,6 +131,7 @@ struct mpm_handle {
     bool envp_dirty = true;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     bool use_graphs = true;
+    Tape tape;
 };
 
 namespace {
@@ -224,10 +215,6 @@ void fill_frames(mpm_handle *h, int first, int nsub, int total, int tstride, Too
     for (int e = 0; e < h->n_envs; ++e)
         for (int t = 0; t < tstride; ++t) {
             const HostTool &tl = h->tools[(size_t)e * MPM_MAX_TOOLS + t];
-            const Quat q0 = qexp_rotvec(tl.cur + 3), q1 = qexp_rotvec(tl.tgt + 3);
-            const Quat dq = qmul(q1, Quat{q0.w, -q0.x, -q0.y, -q0.z});
-            double phi[3];
-            qlog_rotvec(dq, phi);
             const HostField *fd = tl.kind == MPM_TOOL_SAMPLED ? &h->fields[(size_t)tl.field] : nullptr;
             double reach = 0.0;
             if (tl.kind == MPM_TOOL_CAPSULE) {
@@ -252,14 +239,13 @@ void fill_frames(mpm_handle *h, int first, int nsub, int total, int tstride, Too
                 std::memset(&f, 0, sizeof f);
                 f.kind = tl.kind;
                 if (tl.kind == MPM_TOOL_NONE) continue;
-                const double rs[3] = {s * phi[0], s * phi[1], s * phi[2]};
-                double R[9];
-                qmatrix(qmul(qexp_rotvec(rs), q0), R);
+                double R[9], T[3], u[3], w[3];
+                call_frame(tl.cur, tl.tgt, s, span, R, T, u, w);
                 for (int i = 0; i < 9; ++i) f.R[i] = (float)R[i];
                 for (int a = 0; a < 3; ++a) {
-                    f.T[a] = (float)(tl.cur[a] + s * (tl.tgt[a] - tl.cur[a]));
-                    f.u[a] = (float)((tl.tgt[a] - tl.cur[a]) / span);
-                    f.w[a] = (float)(phi[a] / span);
+                    f.T[a] = (float)T[a];
+                    f.u[a] = (float)u[a];
+                    f.w[a] = (float)w[a];
                     f.dims[a] = (float)(fd ? fd->origin[a] : tl.dims[a]);
                 }
                 if (fd) {
@@ -900,6 +886,251 @@ mpm_status mpm_read_order(mpm_handle *h, uint32_t *ids, uint32_t *keys) {
     }
     if (w != (size_t)h->n) return fail(MPM_ERR_STATE, "run tables list %zu of %lld particles", w, (long long)h->n);
     return mpm_synchronize(h);
+}
+
+}  // extern "C"
+
+// ================================================== differentiable rollout
+
+namespace {
+
+void image_views(float *base, int64_t n, PState &S, VCState &V) {
+    const size_t n4 = 4 * (size_t)n;
+    S.xi = reinterpret_cast<float4 *>(base);
+    S.f0 = reinterpret_cast<float4 *>(base + n4);
+    S.f1 = reinterpret_cast<float4 *>(base + 2 * n4);
+    V.vc0 = reinterpret_cast<float4 *>(base + 3 * n4);
+    V.vc1 = reinterpret_cast<float4 *>(base + 4 * n4);
+    V.vc2 = reinterpret_cast<float4 *>(base + 5 * n4);
+    S.f2 = base + 6 * n4;
+}
+
+mpm_status live_to_image(mpm_handle *h, float *img) {
+    PState S;
+    VCState V;
+    image_views(img, h->n, S, V);
+    const size_t n = (size_t)h->n;
+    const PState &L = h->fb.P[0];
+    CK(cudaMemcpyAsync(S.xi, L.xi, 16 * n, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(S.f0, L.f0, 16 * n, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(S.f1, L.f1, 16 * n, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(S.f2, L.f2, 4 * n, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(V.vc0, h->fb.vc.vc0, 16 * n, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(V.vc1, h->fb.vc.vc1, 16 * n, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(V.vc2, h->fb.vc.vc2, 16 * n, cudaMemcpyDeviceToDevice, h->stream));
+    return MPM_OK;
+}
+
+// One split-pipeline sub-step of state (S, V) with grid G (P2G, grid
+// operation, G2P); Gsave, if given, receives the grid the grid operation read.
+mpm_status split_substep(mpm_handle *h, const PState &S, const VCState &V, float4 *G, float4 *Gsave,
+                         const ToolFrame *frames) {
+    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+    const uint32_t n = (uint32_t)h->n;
+    CK(cudaMemsetAsync(G, 0, sizeof(float4) * nn, h->stream));
+    launch_p2g_scatter(h->P, S, V, n, G, h->fb.ctrl, h->elem_grid, h->stream);
+    if (Gsave) CK(cudaMemcpyAsync(Gsave, G, sizeof(float4) * nn, cudaMemcpyDeviceToDevice, h->stream));
+    launch_grid_update_dense(h->P, G, frames, h->elem_grid, h->stream);
+    launch_g2p_split(h->P, S, V, n, G, h->fb.ctrl, h->elem_grid, h->stream);
+    return MPM_OK;
+}
+
+template <typename T>
+mpm_status ensure(mpm_handle *h, T **buf, size_t *cap, size_t count) {
+    if (*cap >= count && *buf) return MPM_OK;
+    mpm_status st = dalloc_t(h, buf, count);   // a smaller earlier buffer stays with the handle until destroy
+    if (st == MPM_OK) *cap = count;
+    return st;
+}
+
+mpm_status copy_in(float *dst, const float *src, size_t count, int on_device, cudaStream_t st) {
+    if (!src) {
+        CK(cudaMemsetAsync(dst, 0, sizeof(float) * count, st));
+        return MPM_OK;
+    }
+    CK(cudaMemcpyAsync(dst, src, sizeof(float) * count, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       st));
+    return MPM_OK;
+}
+
+mpm_status copy_out(float *dst, const float *src, size_t count, int on_device, cudaStream_t st) {
+    if (!dst) return MPM_OK;
+    CK(cudaMemcpyAsync(dst, src, sizeof(float) * count, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       st));
+    return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *poses, int32_t checkpoint_every) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (is_fused(h) || h->n_envs != 1)
+        return fail(MPM_ERR_STATE, "mpm_tape_record needs a split-pipeline handle with one environment");
+    if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
+    if (n_substeps < 1) return fail(MPM_ERR_ARG, "n_substeps must be >= 1");
+    if (checkpoint_every < 1) return fail(MPM_ERR_ARG, "checkpoint_every must be >= 1");
+    const int nt = tool_stride(h);
+    if (nt > 0 && !poses) return fail(MPM_ERR_ARG, "NULL poses");
+    for (size_t i = 0; i < (size_t)n_substeps * nt * 6; ++i)
+        if (!std::isfinite(poses[i])) return fail(MPM_ERR_ARG, "non-finite pose");
+    if ((st = poll_error(h, false)) != MPM_OK) return st;
+    Tape &tp = h->tape;
+    tp.valid = false;
+    const int64_t n = h->n;
+    const int ck = std::min(checkpoint_every, n_substeps);
+    const int nck = (n_substeps + ck - 1) / ck;
+    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+    tp.image = 24 * (size_t)n + (((size_t)n + 3) & ~size_t(3));
+    if ((st = ensure(h, &tp.ckpt, &tp.cap_ckpt, tp.image * nck)) != MPM_OK) return st;
+    if ((st = ensure(h, &tp.seg, &tp.cap_seg, tp.image * ck)) != MPM_OK) return st;
+    if ((st = ensure(h, &tp.seg_grid, &tp.cap_grid, nn * ck)) != MPM_OK) return st;
+    size_t one = nn;
+    if ((st = ensure(h, &tp.gv, &one, nn)) != MPM_OK) return st;
+    one = nn;
+    if ((st = ensure(h, &tp.gbar, &one, nn)) != MPM_OK) return st;
+    if ((st = ensure(h, &tp.abar, &tp.cap_abar, 24 * (size_t)n)) != MPM_OK) return st;
+    if ((st = ensure(h, &tp.frames, &tp.cap_frames, (size_t)n_substeps * std::max(nt, 1))) != MPM_OK) return st;
+    if ((st = ensure(h, &tp.red, &tp.cap_red, 2 + (size_t)n_substeps * nt * 18)) != MPM_OK) return st;
+    if ((st = upload_env_params(h)) != MPM_OK) return st;
+    // frames: one sub-step per pose, from each tool's current pose
+    tp.pose_init.assign((size_t)nt * 6, 0.0);
+    tp.poses.assign(poses, poses + (size_t)n_substeps * nt * 6);
+    for (int t = 0; t < nt; ++t) std::memcpy(&tp.pose_init[6 * t], h->tools[t].cur, 6 * sizeof(double));
+    std::vector<ToolFrame> hf((size_t)n_substeps * std::max(nt, 1));
+    for (int k = 0; k < n_substeps && nt > 0; ++k) {
+        for (int t = 0; t < nt; ++t) std::memcpy(h->tools[t].tgt, poses + ((size_t)k * nt + t) * 6, 6 * sizeof(double));
+        fill_frames(h, 0, 1, 1, nt, &hf[(size_t)k * nt]);
+        for (int t = 0; t < nt; ++t) std::memcpy(h->tools[t].cur, h->tools[t].tgt, 6 * sizeof(double));
+    }
+    if (nt > 0) CK(cudaMemcpy(tp.frames, hf.data(), sizeof(ToolFrame) * hf.size(), cudaMemcpyHostToDevice));
+    tp.E = h->env_E[0];
+    tp.nu = h->env_nu[0];
+    for (int k = 0; k < n_substeps; ++k) {
+        if (k % ck == 0 && (st = live_to_image(h, tp.ckpt + (size_t)(k / ck) * tp.image)) != MPM_OK) return st;
+        if ((st = split_substep(h, h->fb.P[0], h->fb.vc, h->fb.G[0], nullptr, tp.frames + (size_t)k * nt)) != MPM_OK)
+            return st;
+    }
+    CK(cudaGetLastError());
+    h->taken += n_substeps;
+    tp.nsub = n_substeps;
+    tp.ck = ck;
+    tp.ntools = nt;
+    tp.n = n;
+    tp.valid = true;
+    return enqueue_error_copy(h);
+}
+
+mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_bar, const float *F_bar,
+                             const float *C_bar, int on_device, double *grad_material, double *grad_poses,
+                             float *x0_bar, float *v0_bar, float *F0_bar, float *C0_bar) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    Tape &tp = h->tape;
+    if (!tp.valid || tp.n != h->n) return fail(MPM_ERR_STATE, "no recorded rollout (mpm_tape_record) for this state");
+    if (tool_stride(h) != tp.ntools || h->env_E[0] != tp.E || h->env_nu[0] != tp.nu)
+        return fail(MPM_ERR_STATE, "tools or material changed since mpm_tape_record");
+    if ((st = poll_error(h, false)) != MPM_OK) return st;
+    const int64_t n = tp.n;
+    const int nt = tp.ntools;
+    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+    cudaStream_t s = h->stream;
+    AdjState A;
+    A.x = tp.abar;
+    A.v = tp.abar + 3 * (size_t)n;
+    A.C = tp.abar + 6 * (size_t)n;
+    A.F = tp.abar + 15 * (size_t)n;
+    if ((st = copy_in(A.x, x_bar, 3 * (size_t)n, on_device, s)) != MPM_OK) return st;
+    if ((st = copy_in(A.v, v_bar, 3 * (size_t)n, on_device, s)) != MPM_OK) return st;
+    if ((st = copy_in(A.F, F_bar, 9 * (size_t)n, on_device, s)) != MPM_OK) return st;
+    if ((st = copy_in(A.C, C_bar, 9 * (size_t)n, on_device, s)) != MPM_OK) return st;
+    const size_t nred = 2 + (size_t)tp.nsub * nt * 18;
+    CK(cudaMemsetAsync(tp.red, 0, sizeof(double) * nred, s));
+    const int nck = (tp.nsub + tp.ck - 1) / tp.ck;
+    for (int sg = nck - 1; sg >= 0; --sg) {
+        const int c0 = sg * tp.ck, len = std::min(tp.ck, tp.nsub - c0);
+        CK(cudaMemcpyAsync(tp.seg, tp.ckpt + (size_t)sg * tp.image, sizeof(float) * tp.image, cudaMemcpyDeviceToDevice,
+                           s));
+        // replay the segment, keeping every state and the grid each grid operation read
+        for (int j = 0; j < len; ++j) {
+            PState Sj;
+            VCState Vj;
+            image_views(tp.seg + (size_t)j * tp.image, n, Sj, Vj);
+            float4 *Gj = tp.seg_grid + (size_t)j * nn;
+            if (j + 1 < len) {
+                float *next = tp.seg + (size_t)(j + 1) * tp.image;
+                CK(cudaMemcpyAsync(next, tp.seg + (size_t)j * tp.image, sizeof(float) * tp.image,
+                                   cudaMemcpyDeviceToDevice, s));
+                PState Sn;
+                VCState Vn;
+                image_views(next, n, Sn, Vn);
+                if ((st = split_substep(h, Sn, Vn, tp.gv, Gj, tp.frames + (size_t)(c0 + j) * nt)) != MPM_OK) return st;
+            } else {
+                CK(cudaMemsetAsync(Gj, 0, sizeof(float4) * nn, s));
+                launch_p2g_scatter(h->P, Sj, Vj, (uint32_t)n, Gj, h->fb.ctrl, h->elem_grid, s);
+            }
+        }
+        // reverse the segment's sub-steps
+        for (int j = len - 1; j >= 0; --j) {
+            const int k = c0 + j;
+            PState Sj;
+            VCState Vj;
+            image_views(tp.seg + (size_t)j * tp.image, n, Sj, Vj);
+            const float4 *Gj = tp.seg_grid + (size_t)j * nn;
+            const ToolFrame *fr = tp.frames + (size_t)k * nt;
+            CK(cudaMemcpyAsync(tp.gv, Gj, sizeof(float4) * nn, cudaMemcpyDeviceToDevice, s));
+            launch_grid_update_dense(h->P, tp.gv, fr, h->elem_grid, s);
+            CK(cudaMemsetAsync(tp.gbar, 0, sizeof(float4) * nn, s));
+            launch_adj_g2p(h->P, Sj, (uint32_t)n, tp.gv, A, tp.gbar, h->elem_grid, s);
+            launch_adj_grid(h->P, Gj, fr, tp.gbar, tp.red + 2 + (size_t)k * nt * 18, h->elem_grid, s);
+            launch_adj_p2g(h->P, Sj, Vj, (uint32_t)n, tp.gbar, A, tp.red, h->elem_grid, s);
+        }
+    }
+    CK(cudaGetLastError());
+    if ((st = copy_out(x0_bar, A.x, 3 * (size_t)n, on_device, s)) != MPM_OK) return st;
+    if ((st = copy_out(v0_bar, A.v, 3 * (size_t)n, on_device, s)) != MPM_OK) return st;
+    if ((st = copy_out(F0_bar, A.F, 9 * (size_t)n, on_device, s)) != MPM_OK) return st;
+    if ((st = copy_out(C0_bar, A.C, 9 * (size_t)n, on_device, s)) != MPM_OK) return st;
+    std::vector<double> red(nred);
+    CK(cudaMemcpyAsync(red.data(), tp.red, sizeof(double) * nred, cudaMemcpyDeviceToHost, s));
+    if ((st = enqueue_error_copy(h)) != MPM_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    if ((st = poll_error(h, true)) != MPM_OK) return st;
+    if (grad_material) {   // Eq. 6 backwards
+        const double E = tp.E, nu = tp.nu, D = (1.0 + nu) * (1.0 - 2.0 * nu);
+        grad_material[0] = red[0] / (2.0 * (1.0 + nu)) + red[1] * nu / D;
+        grad_material[1] = -red[0] * E / (2.0 * (1.0 + nu) * (1.0 + nu)) + red[1] * E * (1.0 + 2.0 * nu * nu) / (D * D);
+    }
+    if (grad_poses) {
+        std::fill(grad_poses, grad_poses + (size_t)tp.nsub * nt * 6, 0.0);
+        const double span = (double)h->cfg.dt;
+        for (int k = 0; k < tp.nsub; ++k)
+            for (int t = 0; t < nt; ++t) {
+                if (h->tools[t].kind == MPM_TOOL_NONE) continue;
+                const double *fb = &red[2 + ((size_t)k * nt + t) * 18];
+                const double *p0 = k == 0 ? &tp.pose_init[6 * t] : &tp.poses[((size_t)(k - 1) * nt + t) * 6];
+                const double *p1 = &tp.poses[((size_t)k * nt + t) * 6];
+                Dual<12> a[6], b[6], R[9], T[3], u[3], w[3];
+                for (int i = 0; i < 6; ++i) {
+                    a[i] = Dual<12>(p0[i]);
+                    a[i].d[i] = 1.0;
+                    b[i] = Dual<12>(p1[i]);
+                    b[i].d[6 + i] = 1.0;
+                }
+                call_frame(a, b, 1.0, span, R, T, u, w);
+                const Dual<12> *fr[18] = {&R[0], &R[1], &R[2], &R[3], &R[4], &R[5], &R[6], &R[7], &R[8],
+                                          &T[0], &T[1], &T[2], &u[0], &u[1], &u[2], &w[0], &w[1], &w[2]};
+                double g[12] = {};
+                for (int f = 0; f < 18; ++f)
+                    for (int i = 0; i < 12; ++i) g[i] += fb[f] * fr[f]->d[i];
+                if (k > 0)
+                    for (int i = 0; i < 6; ++i) grad_poses[((size_t)(k - 1) * nt + t) * 6 + i] += g[i];
+                for (int i = 0; i < 6; ++i) grad_poses[((size_t)k * nt + t) * 6 + i] += g[6 + i];
+            }
+    }
+    return MPM_OK;
 }
 
 }  // extern "C"

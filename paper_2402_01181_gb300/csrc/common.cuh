@@ -244,6 +244,39 @@ __device__ __forceinline__ float tool_sdf(int kind, const float *dims, float px,
     return qm;
 }
 
+// z-buffer of Sec. III-C at a world node position: the closest tool (lowest
+// index on ties), its distance dmin, the unit normal n_ref and the node
+// position p_ref in that tool's frame (Eq. 11).  Tools whose reach the node
+// is beyond are skipped: their distance is surely >= theta.  Returns -1 if no
+// tool is within reach.
+__device__ __forceinline__ int nearest_tool(float xw, float yw, float zw, const ToolFrame *tools, int ntools,
+                                            float &dmin, float &nbx, float &nby, float &nbz, float &pbx,
+                                            float &pby, float &pbz) {
+    dmin = 3.0e38f;
+    nbx = nby = nbz = 0.f;
+    pbx = pby = pbz = 0.f;
+    int id = -1;
+    for (int t = 0; t < ntools; ++t) {
+        const ToolFrame &tf = tools[t];
+        if (tf.kind < 0) continue;
+        const float rx = xw - tf.T[0], ry = yw - tf.T[1], rz = zw - tf.T[2];
+        if (rx * rx + ry * ry + rz * rz > tf.reach2) continue;   // surely d >= theta
+        // Eq. 11: x_ref = R^T (x - T)
+        const float px = tf.R[0] * rx + tf.R[3] * ry + tf.R[6] * rz;
+        const float py = tf.R[1] * rx + tf.R[4] * ry + tf.R[7] * rz;
+        const float pz = tf.R[2] * rx + tf.R[5] * ry + tf.R[8] * rz;
+        float nx, ny, nz, d;
+        if (tf.kind == 2) {
+            const float4 s = sampled_sdf(tf.sdf, tf.res, tf.inv_h, tf.dims[0], tf.dims[1], tf.dims[2], px, py, pz);
+            d = s.x; nx = s.y; ny = s.z; nz = s.w;
+        } else {
+            d = tool_sdf(tf.kind, tf.dims, px, py, pz, nx, ny, nz);
+        }
+        if (d < dmin) { dmin = d; id = t; nbx = nx; nby = ny; nbz = nz; pbx = px; pby = py; pbz = pz; }
+    }
+    return id;
+}
+
 // Grid operation of one node (i,j,k): Eq. 7 where m > 0, gravity, tool
 // contact with the closest tool (z-buffer merge; Eqs. 11, 15-19 with the
 // friction clamped at zero tangential speed), then sticky walls.
@@ -255,26 +288,8 @@ __device__ __forceinline__ float3 grid_node_update(float m, float mvx, float mvy
     float vz = mvz / m + P.dt * P.gz;
     if (ntools > 0) {
         const float xw = i * P.dx, yw = j * P.dx, zw = k * P.dx;
-        float dmin = 3.0e38f, nbx = 0.f, nby = 0.f, nbz = 0.f;
-        int id = -1;
-        for (int t = 0; t < ntools; ++t) {
-            const ToolFrame &tf = tools[t];
-            if (tf.kind < 0) continue;
-            const float rx = xw - tf.T[0], ry = yw - tf.T[1], rz = zw - tf.T[2];
-            if (rx * rx + ry * ry + rz * rz > tf.reach2) continue;   // surely d >= theta
-            // Eq. 11: x_ref = R^T (x - T)
-            const float px = tf.R[0] * rx + tf.R[3] * ry + tf.R[6] * rz;
-            const float py = tf.R[1] * rx + tf.R[4] * ry + tf.R[7] * rz;
-            const float pz = tf.R[2] * rx + tf.R[5] * ry + tf.R[8] * rz;
-            float nx, ny, nz, d;
-            if (tf.kind == 2) {
-                const float4 s = sampled_sdf(tf.sdf, tf.res, tf.inv_h, tf.dims[0], tf.dims[1], tf.dims[2], px, py, pz);
-                d = s.x; nx = s.y; ny = s.z; nz = s.w;
-            } else {
-                d = tool_sdf(tf.kind, tf.dims, px, py, pz, nx, ny, nz);
-            }
-            if (d < dmin) { dmin = d; id = t; nbx = nx; nby = ny; nbz = nz; }
-        }
+        float dmin, nbx, nby, nbz, pbx, pby, pbz;
+        const int id = nearest_tool(xw, yw, zw, tools, ntools, dmin, nbx, nby, nbz, pbx, pby, pbz);
         if (id >= 0 && dmin < P.theta) {
             const ToolFrame &tf = tools[id];
             const float nx = tf.R[0] * nbx + tf.R[1] * nby + tf.R[2] * nbz;

@@ -25,6 +25,25 @@ void launch_grid_to_dense(int n, int nb, int n_envs, const float4 *G, float4 *ou
 void launch_grid_velocity_dense(const DevParams &P, const float4 *G, const ToolFrame *tools, float *out, int grid,
                                 cudaStream_t st);
 
+// kernels_adjoint.cu: reverse mode of one split-pipeline sub-step.
+// Adjoint of the particle state, row-major per particle (load order).
+struct AdjState {
+    float *x;   // n x 3
+    float *v;   // n x 3
+    float *C;   // n x 9
+    float *F;   // n x 9
+};
+// Gv: grid after the forward grid operation (.yzw = velocity); Gb zeroed on
+// entry, receives dL/d(grid velocity) in .yzw.
+void launch_adj_g2p(const DevParams &P, const PState &S, uint32_t n, const float4 *Gv, const AdjState &A, float4 *Gb,
+                    int grid, cudaStream_t st);
+// G: the (m, mv) grid the forward grid operation read; Gb in: velocity
+// adjoint, out: (dL/dm, dL/dmv); tool_bar: ntools x 18 doubles accumulated.
+void launch_adj_grid(const DevParams &P, const float4 *G, const ToolFrame *tools, float4 *Gb, double *tool_bar,
+                     int grid, cudaStream_t st);
+void launch_adj_p2g(const DevParams &P, const PState &S, const VCState &V, uint32_t n, const float4 *Gb,
+                    const AdjState &A, double *lame_bar, int grid, cudaStream_t st);
+
 // kernels_sort.cu: stable counting sort of particles by grid block at load.
 struct SortScratch {
     uint32_t *keys;     // n

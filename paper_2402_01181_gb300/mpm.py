@@ -83,6 +83,9 @@ SIGNATURES = [
                                           ct.c_void_p]),
     ("mpm_add_sampled_field", ct.c_int, [ct.c_void_p, ct.c_int32, _DP, ct.c_double, ct.c_void_p, ct.c_int,
                                          ct.POINTER(ct.c_int32)]),
+    ("mpm_tape_record", ct.c_int, [ct.c_void_p, ct.c_int32, _DP, ct.c_int32]),
+    ("mpm_tape_backward", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
+                                     _DP, _DP, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
 ]
 
 
@@ -120,6 +123,8 @@ mpm_grid_velocity = lib.mpm_grid_velocity
 mpm_read_order = lib.mpm_read_order
 mpm_block_sort_noalloc = lib.mpm_block_sort_noalloc
 mpm_add_sampled_field = lib.mpm_add_sampled_field
+mpm_tape_record = lib.mpm_tape_record
+mpm_tape_backward = lib.mpm_tape_backward
 
 
 def mpm_last_error() -> str:
@@ -176,6 +181,7 @@ class Sim:
         self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
         self._keep = []
         self._fields = {}
+        self.tape_shape = (0,)
         if use_torch_allocator:
             def _alloc(nbytes, stream, ctx):
                 try:
@@ -277,6 +283,43 @@ class Sim:
         p = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(6))
         s = self._shape_for(shape, field)
         check(mpm_set_tool_pose(self.h, int(tool_id), p.ctypes.data_as(_DP), s.ctypes.data_as(_FP)))
+
+    def tape_record(self, poses, checkpoint_every=50):
+        """Record a rollout of len(poses) sub-steps, poses (K, n_tools, 6):
+        the pose of every tool at the end of each sub-step."""
+        p = np.ascontiguousarray(np.asarray(poses, dtype=np.float64))
+        K = p.shape[0] if p.ndim > 0 else 0
+        check(mpm_tape_record(self.h, int(K), p.ctypes.data_as(_DP), int(checkpoint_every)))
+        self.tape_shape = p.shape
+
+    def tape_backward(self, x_bar=None, v_bar=None, F_bar=None, C_bar=None, want_state=False):
+        """Reverse mode of the recorded rollout from dL/d(final state) (torch
+        CUDA tensors or None).  Returns dict(E, nu, poses[, x, v, F, C])."""
+        torch = self._torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def arg(t, cols):
+            if t is None:
+                return None, ct.c_void_p()
+            t = t.detach().to(device=dev, dtype=torch.float32).contiguous().reshape(self.n, cols)
+            return t, ct.c_void_p(t.data_ptr())
+
+        keep = [arg(x_bar, 3), arg(v_bar, 3), arg(F_bar, 9), arg(C_bar, 9)]
+        gm = np.zeros(2)
+        gp = np.zeros(self.tape_shape if len(self.tape_shape) == 3 else (0,))
+        outs = {}
+        ptrs = []
+        for name, cols in (("x", 3), ("v", 3), ("F", 9), ("C", 9)):
+            if want_state:
+                outs[name] = torch.empty((self.n, cols), dtype=torch.float32, device=dev)
+                ptrs.append(ct.c_void_p(outs[name].data_ptr()))
+            else:
+                ptrs.append(ct.c_void_p())
+        check(mpm_tape_backward(self.h, keep[0][1], keep[1][1], keep[2][1], keep[3][1], 1, gm.ctypes.data_as(_DP),
+                                gp.ctypes.data_as(_DP) if gp.size else None, *ptrs))
+        res = {"E": float(gm[0]), "nu": float(gm[1]), "poses": gp}
+        res.update(outs)
+        return res
 
     def step(self, n_substeps=1):
         check(mpm_step(self.h, int(n_substeps)))

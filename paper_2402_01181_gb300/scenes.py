@@ -308,6 +308,37 @@ def slab30k_sdf(seed: int = 0, res: int = 256) -> Scene:
     return sc
 
 
+@dataclass
+class DiffCase:
+    """A differentiable-rollout workload: the scene, the pose stream of its
+    tool (pose_init, then poses[k, t] at the end of sub-step k), and the
+    perturbed stream and material a target rollout uses."""
+    scene: Scene
+    pose_init: np.ndarray              # (n_tools, 6)
+    poses: np.ndarray                  # (K, n_tools, 6)
+    target_poses: np.ndarray           # (K, n_tools, 6)
+    target_E: float
+    target_nu: float
+    checkpoint: int
+
+
+def slab30k_diff(seed: int = 0, steps: int = 500, checkpoint: int = 50, first: int = 0) -> DiffCase:
+    """The slab30k scene (at rest) over sub-steps first .. first+steps-1 of
+    its tool script (from sub-step 0 the capsule descends onto the slab,
+    touching it near sub-step 100, and presses in), the rollout checkpointed
+    every `checkpoint` sub-steps; the target uses E = 1.2e4, nu = 0.33 and the pose
+    stream shifted by one seeded N(0, 1e-3) draw per pose entry (m, rad),
+    the same at every sub-step, so that the target tool moves as smoothly as
+    the original."""
+    sc = slab30k(seed)
+    tool = sc.tools[0]
+    pose_init = tool.pose(first - 1)[None, :]
+    poses = np.stack([tool.pose(first + k) for k in range(steps)])[:, None, :]
+    rng = np.random.default_rng(seed + 12345)
+    target = poses + rng.normal(0.0, 1e-3, size=(1, 1, 6))
+    return DiffCase(sc, pose_init, poses, target, 1.2e4, 0.33, checkpoint)
+
+
 SCENES = {
     "cube8k": cube8k,
     "slab30k": slab30k,

@@ -1,0 +1,238 @@
+"""The differentiable rollout on the GPU (mpm_tape_record / mpm_tape_backward,
+and the torch.autograd binding) against the FP64 oracle's adjoint, which is
+pinned by central differences in test_oracle_adjoint_pins.py.
+
+Tolerances (FP32 reverse mode against FP64): one sub-step, element by
+element, 2e-4 of each block's largest magnitude (particles whose stencil
+touches a node within 1e-5 of a branch point are left out and counted);
+material gradients 1e-3 relative; pose gradients 2e-3 of the largest entry.
+Rollouts of many sub-steps compare the summed gradients at 1e-2 (two tools,
+30 sub-steps) and 3e-2 / 5e-2 (the slab: its loss is a mean of squared
+gaps of ~1e-5 m, while FP32 positions near 0.5 resolve 6e-8 m and carry
+the rounding of hundreds of sub-steps), and the oracle's own central
+differences confirm the GPU gradient."""
+import numpy as np
+import pytest
+
+import helpers as H
+import test_oracle_adjoint_pins as AP
+from oracle import oracle as O
+from paper_2402_01181_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def M():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2402_01181_gb300 import mpm
+    return mpm
+
+
+def _sim(M, prm, n):
+    cfg = M.make_config(prm.n_grid, prm.dt, prm.E, prm.nu, prm.rho, gravity=tuple(prm.gravity), bound=prm.bound,
+                        theta=prm.theta, friction=prm.friction, pipeline=M.MPM_PIPELINE_SPLIT, max_particles=n)
+    return M.Sim(cfg)
+
+
+def _f32_state(st):
+    return {k: getattr(st, k).astype(np.float32) for k in ("x", "v", "F", "C")}
+
+
+def test_single_substep_adjoint_matches_oracle(M):
+    import torch
+    prm, st, tools, p0, p1 = AP._scene()
+    s32 = _f32_state(st)
+    sim = _sim(M, prm, st.n)
+    sim.load(s32["x"], prm.V0, s32["v"], s32["F"], s32["C"])
+    for t, tool in enumerate(tools):
+        sim.set_tool(t, p0[t], tool.shape)
+    sim.tape_record(p1[None], 1)
+    rng = np.random.default_rng(21)
+    ybar = AP._random_bar(rng, st.n)
+    dev = torch.device("cuda")
+    g = sim.tape_backward(*[torch.tensor(ybar[k], dtype=torch.float32, device=dev) for k in ("x", "v", "F", "C")],
+                          want_state=True)
+    sim.close()
+    ref_state = O.State(s32["x"], s32["v"], s32["C"], s32["F"])
+    frames = AP._frames(tools, p0, p1, prm.dt)
+    ybar32 = {k: ybar[k].astype(np.float32).astype(np.float64) for k in ybar}
+    rbar, lame, tb = O.step_adjoint(prm, ref_state, frames, 2, ybar32)
+    gm, gmv = O.p2g(prm, ref_state.copy())
+    _, contact, margin = O.grid_update(prm, gm, gmv, frames, 2)
+    assert (contact >= 0).sum() > 20
+    skip = H.particles_touching(margin < 1e-5, ref_state.x, prm.n_grid)
+    assert skip.sum() <= 0.02 * st.n
+    keep = ~skip
+    for k in ("x", "v", "F", "C"):
+        got = g[k].cpu().numpy().astype(np.float64)
+        scale = np.abs(rbar[k]).max()
+        err = np.abs(got[keep] - rbar[k][keep]).max() / scale
+        assert err <= 2e-4, (k, err)
+    Eb, nub = O.lame_vjp(prm.E, prm.nu, lame[0], lame[1])
+    assert abs(g["E"] - Eb) <= 1e-3 * abs(Eb), (g["E"], Eb)
+    assert abs(g["nu"] - nub) <= 1e-3 * abs(nub), (g["nu"], nub)
+    for t, tool in enumerate(tools):
+        J = O.frame_jacobian(tool.shape, p0[t], p1[t], prm.dt)
+        ref = J[:, 6:].T @ tb[t]
+        got = g["poses"][0, t]
+        assert np.abs(got - ref).max() <= 2e-3 * np.abs(ref).max(), (t, got, ref)
+
+
+def test_rollout_gradients_match_oracle(M):
+    """30 sub-steps with two moving tools, checkpoints every 8 (a short last
+    segment), loss = mean |x(T) - target|^2, through torch.autograd."""
+    import torch
+    from paper_2402_01181_gb300 import autodiff
+    prm, st, tools, p0, p1 = AP._scene(seed=11)
+    K = 30
+    poses = np.stack([p0 + (k + 1) * 0.5 * (p1 - p0) for k in range(K)])
+    s32 = _f32_state(st)
+    rng = np.random.default_rng(22)
+    target = (st.x + 0.01 * rng.normal(size=st.x.shape)).astype(np.float32)
+    dev = torch.device("cuda")
+    sim = _sim(M, prm, st.n)
+    for t, tool in enumerate(tools):
+        sim.set_tool(t, p0[t], tool.shape)
+    E = torch.tensor(prm.E, dtype=torch.float64, requires_grad=True)
+    nu = torch.tensor(prm.nu, dtype=torch.float64, requires_grad=True)
+    P = torch.tensor(poses, dtype=torch.float64, requires_grad=True)
+    x0 = torch.tensor(s32["x"], device=dev, requires_grad=True)
+    v0 = torch.tensor(s32["v"], device=dev, requires_grad=True)
+    F0 = torch.tensor(s32["F"], device=dev, requires_grad=True)
+    C0 = torch.tensor(s32["C"], device=dev, requires_grad=True)
+    xT, vT, FT, CT = autodiff.rollout(sim, E, nu, P, x0, prm.V0, v0, F0, C0, checkpoint_every=8)
+    loss = ((xT - torch.tensor(target, device=dev)) ** 2).sum(dim=1).mean()
+    loss.backward()
+    sim.close()
+    ref = O.rollout_loss_and_gradients(prm, O.State(s32["x"], s32["v"], s32["C"], s32["F"]), tools, p0, poses,
+                                       target.astype(np.float64), checkpoint=8)
+    assert abs(loss.item() - ref["loss"]) <= 1e-4 * ref["loss"]
+    assert abs(E.grad.item() - ref["E"]) <= 1e-2 * abs(ref["E"]), (E.grad.item(), ref["E"])
+    assert abs(nu.grad.item() - ref["nu"]) <= 1e-2 * abs(ref["nu"]), (nu.grad.item(), ref["nu"])
+    gp = P.grad.numpy()
+    assert np.abs(gp - ref["poses"]).max() <= 1e-2 * np.abs(ref["poses"]).max()
+    for k, got in (("x", x0.grad), ("v", v0.grad), ("F", F0.grad), ("C", C0.grad)):
+        r = ref["state0"][k]
+        assert np.abs(got.cpu().numpy() - r).max() <= 1e-2 * np.abs(r).max(), k
+
+
+def test_slab30k_rollout_gradient_against_oracle_and_differences(M):
+    """The tissue slab pressed by the capsule: 200 sub-steps from the moment
+    the capsule reaches the slab (sub-step 90 of its script; 1 cm of
+    indentation), checkpoints every 50.  The target comes from an FP64 oracle
+    rollout with E = 1.2e4, nu = 0.33 and shifted poses.  The GPU gradients
+    with respect to E, nu and the poses match the oracle's adjoint, and the
+    oracle's central differences of the loss for E and nu.  The loss is
+    small (RMS gap ~1e-5 m) against FP32 positions near 0.5 (resolution 6e-8
+    m), which bounds the GPU's agreement near 1%."""
+    import torch
+    from paper_2402_01181_gb300 import autodiff
+    case = scenes.slab30k_diff(steps=200, checkpoint=50, first=90)
+    sc = case.scene
+    prm = O.OracleParams.from_scene(sc)
+    tools = sc.tools
+    tprm = O.OracleParams(**{**prm.__dict__, "E": case.target_E, "nu": case.target_nu})
+    st0 = O.State(sc.x)
+    tgt_state = st0.copy()
+    tf, nt = O.rollout_frames(tools, case.pose_init, case.target_poses, prm.dt)
+    O.run(tprm, tgt_state, case.poses.shape[0], tf, nt)
+    target = tgt_state.x.astype(np.float32)
+    dev = torch.device("cuda")
+    sim = M.sim_from_scene(sc, pipeline=M.MPM_PIPELINE_SPLIT, load=False)
+    sim.set_tool(0, case.pose_init[0], tools[0].shape)      # placed at the start of the stream
+    E = torch.tensor(prm.E, dtype=torch.float64, requires_grad=True)
+    nu = torch.tensor(prm.nu, dtype=torch.float64, requires_grad=True)
+    P = torch.tensor(case.poses, dtype=torch.float64, requires_grad=True)
+    x0 = torch.tensor(sc.x, device=dev)
+    xT, _, _, _ = autodiff.rollout(sim, E, nu, P, x0, sc.particle_volume, checkpoint_every=case.checkpoint)
+    loss = ((xT - torch.tensor(target, device=dev)) ** 2).sum(dim=1).mean()
+    loss.backward()
+    sim.close()
+    ref = O.rollout_loss_and_gradients(prm, st0, tools, case.pose_init, case.poses, target.astype(np.float64),
+                                       checkpoint=case.checkpoint)
+    assert abs(loss.item() - ref["loss"]) <= 2e-2 * ref["loss"], (loss.item(), ref["loss"])
+    assert abs(E.grad.item() - ref["E"]) <= 3e-2 * abs(ref["E"]), (E.grad.item(), ref["E"])
+    assert abs(nu.grad.item() - ref["nu"]) <= 3e-2 * abs(ref["nu"]), (nu.grad.item(), ref["nu"])
+    gp = P.grad.numpy()
+    assert np.abs(gp - ref["poses"]).max() <= 5e-2 * np.abs(ref["poses"]).max()
+
+    def loss_at(E_, nu_, poses_):
+        p = O.OracleParams(**{**prm.__dict__, "E": E_, "nu": nu_})
+        s = st0.copy()
+        fr, n_ = O.rollout_frames(tools, case.pose_init, poses_, prm.dt)
+        O.run(p, s, poses_.shape[0], fr, n_)
+        return float(np.mean(np.sum((s.x - target) ** 2, axis=1)))
+
+    hE, hn = 1e-3 * prm.E, 1e-3 * prm.nu
+    fdE = (loss_at(prm.E + hE, prm.nu, case.poses) - loss_at(prm.E - hE, prm.nu, case.poses)) / (2 * hE)
+    fdn = (loss_at(prm.E, prm.nu + hn, case.poses) - loss_at(prm.E, prm.nu - hn, case.poses)) / (2 * hn)
+    assert abs(E.grad.item() - fdE) <= 5e-2 * abs(fdE), (E.grad.item(), fdE)
+    assert abs(nu.grad.item() - fdn) <= 5e-2 * abs(fdn), (nu.grad.item(), fdn)
+
+
+def test_tape_contract(M):
+    import torch
+    sc = scenes.cube8k()
+    fused = M.sim_from_scene(sc)
+    poses = np.zeros((3, 0, 6))
+    with pytest.raises(M.MPMError) as e:
+        fused.tape_record(poses, 1)
+    assert e.value.status == M.MPM_ERR_STATE
+    fused.close()
+    sim = M.sim_from_scene(sc, pipeline=M.MPM_PIPELINE_SPLIT)
+    with pytest.raises(M.MPMError) as e:
+        sim.tape_backward(torch.zeros((sc.n, 3), device="cuda"))
+    assert e.value.status == M.MPM_ERR_STATE
+    with pytest.raises(M.MPMError) as e:
+        sim.tape_record(poses, 0)
+    assert e.value.status == M.MPM_ERR_ARG
+    sim.tape_record(poses, 2)
+    out = sim.read()
+    ref = O.State(sc.x)
+    H.oracle_steps(sc, ref, 0, 3)
+    assert np.abs(out["x"] - ref.x).max() <= 1e-3 * sc.dx      # the record steps the state like mpm_step
+    sim.set_env_material(0, sc.E * 2, sc.nu, sc.rho)
+    with pytest.raises(M.MPMError) as e:
+        sim.tape_backward(torch.zeros((sc.n, 3), device="cuda"))
+    assert e.value.status == M.MPM_ERR_STATE
+    sim.close()
+
+
+def test_config5_full_size_gradients_match_oracle(M):
+    """The full differentiable workload the benchmark times: the 30K slab
+    over 500 sub-steps (the capsule descends, touches near sub-step 100 and
+    presses 2 cm in), checkpoints every 50; the target from an FP64 oracle
+    rollout with E = 1.2e4, nu = 0.33 and shifted poses.  The GPU loss and
+    its gradients with respect to E, nu and all 500 x 6 pose entries against
+    the oracle's adjoint."""
+    import torch
+    from paper_2402_01181_gb300 import autodiff
+    case = scenes.slab30k_diff()
+    sc = case.scene
+    prm = O.OracleParams.from_scene(sc)
+    tprm = O.OracleParams(**{**prm.__dict__, "E": case.target_E, "nu": case.target_nu})
+    st0 = O.State(sc.x)
+    tgt_state = st0.copy()
+    tf, nt = O.rollout_frames(sc.tools, case.pose_init, case.target_poses, prm.dt)
+    O.run(tprm, tgt_state, case.poses.shape[0], tf, nt)
+    target = tgt_state.x.astype(np.float32)
+    dev = torch.device("cuda")
+    sim = M.sim_from_scene(sc, pipeline=M.MPM_PIPELINE_SPLIT, load=False)
+    sim.set_tool(0, case.pose_init[0], sc.tools[0].shape)
+    E = torch.tensor(prm.E, dtype=torch.float64, requires_grad=True)
+    nu = torch.tensor(prm.nu, dtype=torch.float64, requires_grad=True)
+    P = torch.tensor(case.poses, dtype=torch.float64, requires_grad=True)
+    xT, _, _, _ = autodiff.rollout(sim, E, nu, P, torch.tensor(sc.x, device=dev), sc.particle_volume,
+                                   checkpoint_every=case.checkpoint)
+    loss = ((xT - torch.tensor(target, device=dev)) ** 2).sum(dim=1).mean()
+    loss.backward()
+    sim.close()
+    ref = O.rollout_loss_and_gradients(prm, st0, sc.tools, case.pose_init, case.poses, target.astype(np.float64),
+                                       checkpoint=case.checkpoint)
+    assert abs(loss.item() - ref["loss"]) <= 2e-2 * ref["loss"], (loss.item(), ref["loss"])
+    assert abs(E.grad.item() - ref["E"]) <= 3e-2 * abs(ref["E"]), (E.grad.item(), ref["E"])
+    assert abs(nu.grad.item() - ref["nu"]) <= 3e-2 * abs(ref["nu"]), (nu.grad.item(), ref["nu"])
+    gp = P.grad.numpy()
+    assert np.abs(gp - ref["poses"]).max() <= 5e-2 * np.abs(ref["poses"]).max()
