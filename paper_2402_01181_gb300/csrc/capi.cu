@@ -70,11 +70,12 @@ struct Tape {
     int nsub = 0, ck = 0, ntools = 0;
     int64_t n = 0;
     size_t image = 0;                 // floats per state image
-    size_t cap_ckpt = 0, cap_seg = 0, cap_frames = 0, cap_red = 0, cap_grid = 0, cap_abar = 0;
+    size_t cap_ckpt = 0, cap_seg = 0, cap_frames = 0, cap_red = 0, cap_grid = 0, cap_vel = 0, cap_abar = 0;
     float *ckpt = nullptr;            // checkpoint images, one per ck sub-steps
     float *seg = nullptr;             // ck images of the segment being reversed
     float4 *seg_grid = nullptr;       // ck grids (m, mv) as the grid operation read them
-    float4 *gv = nullptr;             // grid velocities of the sub-step being reversed
+    float4 *seg_vel = nullptr;        // ck grids (m, v) the grid operation wrote
+    float4 *gv = nullptr;             // scratch grid of the recorded forward pass
     float4 *gbar = nullptr;           // grid adjoint
     float *abar = nullptr;            // particle adjoint: x (3n), v (3n), C (9n), F (9n)
     ToolFrame *frames = nullptr;      // nsub x ntools (device)
@@ -987,6 +988,7 @@ mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *pose
     if ((st = ensure(h, &tp.ckpt, &tp.cap_ckpt, tp.image * nck)) != MPM_OK) return st;
     if ((st = ensure(h, &tp.seg, &tp.cap_seg, tp.image * ck)) != MPM_OK) return st;
     if ((st = ensure(h, &tp.seg_grid, &tp.cap_grid, nn * ck)) != MPM_OK) return st;
+    if ((st = ensure(h, &tp.seg_vel, &tp.cap_vel, nn * ck)) != MPM_OK) return st;
     size_t one = nn;
     if ((st = ensure(h, &tp.gv, &one, nn)) != MPM_OK) return st;
     one = nn;
@@ -1053,12 +1055,16 @@ mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_b
         const int c0 = sg * tp.ck, len = std::min(tp.ck, tp.nsub - c0);
         CK(cudaMemcpyAsync(tp.seg, tp.ckpt + (size_t)sg * tp.image, sizeof(float) * tp.image, cudaMemcpyDeviceToDevice,
                            s));
-        // replay the segment, keeping every state and the grid each grid operation read
+        // replay the segment, keeping every state, the grid each grid operation
+        // read and the velocities it wrote
         for (int j = 0; j < len; ++j) {
             PState Sj;
             VCState Vj;
             image_views(tp.seg + (size_t)j * tp.image, n, Sj, Vj);
-            float4 *Gj = tp.seg_grid + (size_t)j * nn;
+            float4 *Gj = tp.seg_grid + (size_t)j * nn, *Uj = tp.seg_vel + (size_t)j * nn;
+            CK(cudaMemsetAsync(Gj, 0, sizeof(float4) * nn, s));
+            launch_p2g_scatter(h->P, Sj, Vj, (uint32_t)n, Gj, h->fb.ctrl, h->elem_grid, s);
+            launch_grid_update_dense_to(h->P, Gj, Uj, tp.frames + (size_t)(c0 + j) * nt, h->elem_grid, s);
             if (j + 1 < len) {
                 float *next = tp.seg + (size_t)(j + 1) * tp.image;
                 CK(cudaMemcpyAsync(next, tp.seg + (size_t)j * tp.image, sizeof(float) * tp.image,
@@ -1066,10 +1072,7 @@ mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_b
                 PState Sn;
                 VCState Vn;
                 image_views(next, n, Sn, Vn);
-                if ((st = split_substep(h, Sn, Vn, tp.gv, Gj, tp.frames + (size_t)(c0 + j) * nt)) != MPM_OK) return st;
-            } else {
-                CK(cudaMemsetAsync(Gj, 0, sizeof(float4) * nn, s));
-                launch_p2g_scatter(h->P, Sj, Vj, (uint32_t)n, Gj, h->fb.ctrl, h->elem_grid, s);
+                launch_g2p_split(h->P, Sn, Vn, (uint32_t)n, Uj, h->fb.ctrl, h->elem_grid, s);
             }
         }
         // reverse the segment's sub-steps
@@ -1078,12 +1081,10 @@ mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_b
             PState Sj;
             VCState Vj;
             image_views(tp.seg + (size_t)j * tp.image, n, Sj, Vj);
-            const float4 *Gj = tp.seg_grid + (size_t)j * nn;
+            const float4 *Gj = tp.seg_grid + (size_t)j * nn, *Uj = tp.seg_vel + (size_t)j * nn;
             const ToolFrame *fr = tp.frames + (size_t)k * nt;
-            CK(cudaMemcpyAsync(tp.gv, Gj, sizeof(float4) * nn, cudaMemcpyDeviceToDevice, s));
-            launch_grid_update_dense(h->P, tp.gv, fr, h->elem_grid, s);
             CK(cudaMemsetAsync(tp.gbar, 0, sizeof(float4) * nn, s));
-            launch_adj_g2p(h->P, Sj, (uint32_t)n, tp.gv, A, tp.gbar, h->elem_grid, s);
+            launch_adj_g2p(h->P, Sj, (uint32_t)n, Uj, A, tp.gbar, h->elem_grid, s);
             launch_adj_grid(h->P, Gj, fr, tp.gbar, tp.red + 2 + (size_t)k * nt * 18, h->elem_grid, s);
             launch_adj_p2g(h->P, Sj, Vj, (uint32_t)n, tp.gbar, A, tp.red, h->elem_grid, s);
         }

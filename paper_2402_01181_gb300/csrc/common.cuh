@@ -91,18 +91,27 @@ struct BlockTab {
 };
 
 // Control words living in device memory.
+// The counters every CTA of a fused launch updates sit on separate 128-byte
+// lines, so that their atomics are served by different L2 slices at once.
 struct Ctrl {
-    uint32_t step;          // sub-step index (monotonic, starts at 1 after a load)
-    uint32_t done;          // CTAs finished in the current fused launch
-    uint32_t work;          // next work item of the current fused launch
-    uint32_t part_alloc;    // particle slots handed out in the current launch
-    uint32_t chunk_alloc;   // chunk entries handed out in the current launch
-    uint32_t nactive[2];    // active-block list sizes, by sub-step parity
-    uint32_t nclear[3];     // grid clear-list sizes, by sub-step mod 3
+    uint32_t step;              // sub-step index (monotonic, starts at 1 after a load)
     uint32_t n_particles;
-    uint32_t err;           // sticky error bits
-    uint32_t pad[4];
+    uint32_t err;               // sticky error bits
+    uint32_t pad0[29];
+    uint32_t done;              // CTAs finished in the current fused launch
+    uint32_t pad1[31];
+    uint32_t work;              // next work item of the current fused launch
+    uint32_t pad2[31];
+    uint32_t part_alloc;        // particle slots handed out in the current launch
+    uint32_t pad3[31];
+    uint32_t chunk_alloc;       // chunk entries handed out in the current launch
+    uint32_t pad4[31];
+    uint32_t nactive[2];        // active-block list sizes, by sub-step parity
+    uint32_t pad5[30];
+    uint32_t nclear[3];         // grid clear-list sizes, by sub-step mod 3
+    uint32_t pad6[29];
 };
+static_assert(sizeof(Ctrl) == 7 * 128, "Ctrl: one 128-byte line per counter group");
 
 // ----------------------------------------------------------- grid layout
 

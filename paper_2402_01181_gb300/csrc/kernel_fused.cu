@@ -64,13 +64,19 @@ struct FusedSmem {
     float st_f[3][GROUP];
     float st_q[3][GROUP];
     float st_a[9][GROUP];
+    // each thread's particle of the current pass, prefetched with cp.async a pass
+    // ahead (a thread reads and refills only its own slot)
+    float4 pxi[T], pf0[T], pf1[T];
+    float pf2[T];
     uint32_t cand_start[CMAX];     // first slot of each run
     uint32_t cand_pre[CMAX + 1];   // exclusive prefix of run lengths
     uint32_t lane_first[27], lane_off[27];
-    uint32_t wcnt[2][NW][28];      // per pass parity: per-warp direction counts, then offsets
-    uint32_t dstart[28];
+    uint32_t wcnt[2][NW][28];      // per pass parity: per-warp direction counts
     uint32_t ncand, total, out_base, chunk_first, npass, mask, bmax;
 };
+
+// three CTAs per SM: 228 KB of shared memory per SM, 1 KB reserved per CTA
+static_assert(3 * (sizeof(FusedSmem) + 1024) <= 228 * 1024, "shared memory for three CTAs per SM");
 
 __device__ __forceinline__ int dir_dx(int d) { return d % 3 - 1; }
 __device__ __forceinline__ int dir_dy(int d) { return (d / 3) % 3 - 1; }
@@ -90,8 +96,33 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool va
     const int bytes = valid ? 16 : 0;   // 0: fill with zeros, read nothing
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Slot of logical index j among the block's incoming runs (binary search of
+// the runs' exclusive prefix).
+__device__ __forceinline__ uint32_t source_slot(const FusedSmem &s, uint32_t ncand, uint32_t j) {
+    int lo = 0, hi = (int)ncand - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s.cand_pre[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    return s.cand_start[lo] + (j - s.cand_pre[lo]);
+}
+
+// Start copying the particle with logical index j into this thread's slot.
+__device__ __forceinline__ void prefetch_particle(FusedSmem &s, const PState &in, uint32_t ncand, uint32_t j, int tid) {
+    const uint32_t src = source_slot(s, ncand, j);
+    cp_async16(&s.pxi[tid], &in.xi[src], true);
+    cp_async16(&s.pf0[tid], &in.f0[src], true);
+    cp_async16(&s.pf1[tid], &in.f1[src], true);
+    cp_async4(&s.pf2[tid], &in.f2[src]);
+}
 
 // Start copying global block b's grid region of G_k, its inbox, and its
 // environment's material and tool frames into buffer buf.
@@ -291,10 +322,14 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
             }
         }
         __syncthreads();
-        // start copying the next block's inputs; they land while this block computes
-        if (s.items[cb ^ 1] < nact) prefetch_block(s, cb ^ 1, s.bids[cb ^ 1], inbox_in, Gcur, P, tools, tid);
         const uint32_t ncand = s.ncand;
         const uint32_t total = s.total, npass = s.npass, out_base = s.out_base, chunk_first = s.chunk_first;
+        // this thread's particle of the first pass, then the next block's inputs;
+        // both land while this block computes
+        if (npass > 0 && (uint32_t)tid < total) prefetch_particle(s, in, ncand, (uint32_t)tid, tid);
+        cp_async_commit();
+        if (s.items[cb ^ 1] < nact) prefetch_block(s, cb ^ 1, s.bids[cb ^ 1], inbox_in, Gcur, P, tools, tid);
+        else cp_async_commit();
         const int ox = 4 * bx - 1, oy = 4 * by - 1, oz = 4 * bz - 1;   // arena origin
 
         for (uint32_t pass = 0; pass < npass; ++pass) {
@@ -303,17 +338,14 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
             const int slot = (pass & 1) * T + tid;     // staging slot within the group
             int d = 31;
             float nxp = 0.f, nyp = 0.f, nzp = 0.f, idf = 0.f, Fn[9], Cm[9], vx = 0.f, vy = 0.f, vz = 0.f;
+            // this pass's particle is in the slot; the next block's inputs may still be landing
+            if (pass == 0) cp_async_wait_but_one(); else cp_async_wait_all();
+            float4 xi = make_float4(0.f, 0.f, 0.f, 0.f), a0 = xi, a1 = xi;
+            float f2 = 0.f;
+            if (valid) { xi = s.pxi[tid]; a0 = s.pf0[tid]; a1 = s.pf1[tid]; f2 = s.pf2[tid]; }
+            const uint32_t jn = j + T;
             if (valid) {
-                // locate the run holding logical index j
-                int lo = 0, hi = (int)ncand - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s.cand_pre[mid] <= j) lo = mid; else hi = mid - 1;
-                }
-                const uint32_t src = s.cand_start[lo] + (j - s.cand_pre[lo]);
-                const float4 xi = in.xi[src];
-                const float4 a0 = in.f0[src], a1 = in.f1[src];
-                const float F[9] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, in.f2[src]};
+                const float F[9] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, f2};
                 idf = xi.w;
                 // --- G2P from the shared velocities (Eqs. 8-9)
                 int gx, gy, gz;
@@ -363,6 +395,9 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
                 nxp = xi.x + P.dt * vx;
                 nyp = xi.y + P.dt * vy;
                 nzp = xi.z + P.dt * vz;
+                // every value read from the slot has been consumed: refill it with the
+                // next pass's particle
+                if (pass + 1 < npass && jn < total) prefetch_particle(s, in, ncand, jn, tid);
                 if (!finite3(nxp, nyp, nzp)) {
                     err |= kErrNumeric;
                     nxp = xi.x; nyp = xi.y; nzp = xi.z;
@@ -431,29 +466,37 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
             } else {
                 s.st_base[slot] = -1;
             }
-            // --- stable rank by direction within the pass
+            cp_async_commit();
+            // --- stable rank by direction within the pass: per-warp counts, then
+            // every warp derives the offsets it needs from the whole table (one
+            // barrier per pass; warp 0 also publishes the pass's runs)
             const unsigned peers = __match_any_sync(0xffffffffu, d);
             const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
             uint32_t(*wc)[28] = s.wcnt[pass & 1];
             if (valid && rank == 0) wc[warp][d] = __popc(peers);
             __syncthreads();
-            for (int q = tid; q < NW * 28; q += T) (&s.wcnt[(pass + 1) & 1][0][0])[q] = 0u;
-            if (warp == 0) {
-                uint32_t run = 0;
-                if (lane < 27)
-                    for (int w = 0; w < NW; ++w) {
-                        const uint32_t c = wc[w][lane];
-                        wc[w][lane] = run;
-                        run += c;
-                    }
-                uint32_t incl = run;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
+            uint32_t run = 0, before = 0;                 // lane l: pass total and earlier warps' count of direction l
+            if (lane < 27) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const uint32_t c = wc[w][lane];
+                    before += w < warp ? c : 0u;
+                    run += c;
                 }
+            }
+            uint32_t incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t my_off = __shfl_sync(0xffffffffu, incl - run + before, d & 31);
+            // this warp's row of the other parity is next written by this warp, in the
+            // next pass; every warp's reads of it ended before the barrier above
+            if (lane < 28) s.wcnt[(pass + 1) & 1][warp][lane] = 0u;
+            if (warp == 0) {
                 const uint32_t pbase = out_base + pass * T;
                 if (lane < 27) {
-                    s.dstart[lane] = incl - run;
                     cout[chunk_first + pass].run[lane] = make_uint2(pbase + incl - run, run);
                     const int tx = bx + dir_dx(lane), ty = by + dir_dy(lane), tz = bz + dir_dz(lane);
                     if (run > 0u && tx >= 0 && ty >= 0 && tz >= 0 && tx < nb && ty < nb && tz < nb) {
@@ -467,9 +510,8 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
                 const unsigned nz = __ballot_sync(0xffffffffu, lane < 27 && run > 0);
                 if (lane == 0) s.mask |= nz;
             }
-            __syncthreads();
             if (valid) {
-                const uint32_t pos = out_base + pass * T + s.dstart[d] + wc[warp][d] + rank;
+                const uint32_t pos = out_base + pass * T + my_off + rank;
                 out.xi[pos] = make_float4(nxp, nyp, nzp, idf);
                 out.f0[pos] = make_float4(Fn[0], Fn[1], Fn[2], Fn[3]);
                 out.f1[pos] = make_float4(Fn[4], Fn[5], Fn[6], Fn[7]);

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(256) k_p2g_scatter(DevParams P, PState S, VCSt
 
 // ------------------------------------------------------ grid operation
 
-__global__ void __launch_bounds__(256) k_grid_update_dense(DevParams P, float4 *__restrict__ G,
+// Gout may equal Gin (in place).
+__global__ void __launch_bounds__(256) k_grid_update_dense(DevParams P, const float4 *Gin, float4 *Gout,
                                                             const ToolFrame *__restrict__ tools) {
     __shared__ ToolFrame s_tools[kMaxTools];
     const int ntools = P.envp[0].ntools;
@@ -73,16 +74,16 @@ __global__ void __launch_bounds__(256) k_grid_update_dense(DevParams P, float4 *
     __syncthreads();
     const uint32_t total = (uint32_t)P.n * P.n * P.n;
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-        const float4 node = G[g];
+        const float4 node = Gin[g];
         if (!(node.x > 0.0f)) {
-            if (node.y != 0.f || node.z != 0.f || node.w != 0.f) G[g] = make_float4(node.x, 0.f, 0.f, 0.f);
+            if (Gout != Gin || node.y != 0.f || node.z != 0.f || node.w != 0.f) Gout[g] = make_float4(node.x, 0.f, 0.f, 0.f);
             continue;
         }
         const uint32_t b = g >> 6, l = g & 63u;
         const int bx = b % P.nb, by = (b / P.nb) % P.nb, bz = b / (P.nb * P.nb);
         const int i = bx * 4 + (l & 3), j = by * 4 + ((l >> 2) & 3), k = bz * 4 + (l >> 4);
         const float3 v = grid_node_update(node.x, node.y, node.z, node.w, i, j, k, P, s_tools, ntools);
-        G[g] = make_float4(node.x, v.x, v.y, v.z);
+        Gout[g] = make_float4(node.x, v.x, v.y, v.z);
     }
 }
 
@@ -236,7 +237,11 @@ void launch_p2g_scatter(const DevParams &P, const PState &S, const VCState &V, u
     k_p2g_scatter<<<grid, 256, 0, st>>>(P, S, V, n, G, ctrl);
 }
 void launch_grid_update_dense(const DevParams &P, float4 *G, const ToolFrame *tools, int grid, cudaStream_t st) {
-    k_grid_update_dense<<<grid, 256, 0, st>>>(P, G, tools);
+    k_grid_update_dense<<<grid, 256, 0, st>>>(P, G, G, tools);
+}
+void launch_grid_update_dense_to(const DevParams &P, const float4 *Gin, float4 *Gout, const ToolFrame *tools, int grid,
+                                 cudaStream_t st) {
+    k_grid_update_dense<<<grid, 256, 0, st>>>(P, Gin, Gout, tools);
 }
 void launch_g2p_split(const DevParams &P, const PState &S, const VCState &V, uint32_t n, const float4 *G, Ctrl *ctrl,
                       int grid, cudaStream_t st) {

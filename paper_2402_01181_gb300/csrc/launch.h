@@ -15,6 +15,9 @@ void set_last_error(const char *msg);
 void launch_p2g_scatter(const DevParams &P, const PState &S, const VCState &V, uint32_t n, float4 *G, Ctrl *ctrl,
                         int grid, cudaStream_t st);
 void launch_grid_update_dense(const DevParams &P, float4 *G, const ToolFrame *tools, int grid, cudaStream_t st);
+// the grid operation of Gin (m, mv) into Gout (m, v)
+void launch_grid_update_dense_to(const DevParams &P, const float4 *Gin, float4 *Gout, const ToolFrame *tools, int grid,
+                                 cudaStream_t st);
 void launch_g2p_split(const DevParams &P, const PState &S, const VCState &V, uint32_t n, const float4 *G, Ctrl *ctrl,
                       int grid, cudaStream_t st);
 void launch_load_identity(const float *x, const float *v, const float *F, const float *C, uint32_t n, const PState &S,
