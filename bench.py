@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--pipeline", default="fused", choices=["fused", "split"])
     ap.add_argument("--no-secondary", action="store_true", help="skip the 30K slab line")
     ap.add_argument("--no-differentiable", action="store_true", help="skip the differentiable-rollout line")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default fused-kernel configuration")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-environment measurement")
     ap.add_argument("--batch-envs", type=int, default=256)
@@ -150,6 +151,10 @@ def run_gpu_workload(name, args, rank, device, barrier, max_over_ranks, with_e2e
     sim = mpm.sim_from_scene(sc, pipeline=pipe)
     tool_frames = [(t, tool) for t, tool in enumerate(sc.tools)]
     s_next = [0]
+    tuning = None
+    if pipe == mpm.MPM_PIPELINE_FUSED and not args.no_autotune:
+        best, times = sim.autotune(S)          # restores the state it starts from
+        tuning = {"config": best, "name": mpm.KERNEL_CONFIG_NAMES[best], "ms_per_step_by_config": times}
 
     def frame():
         s = s_next[0]
@@ -182,7 +187,7 @@ def run_gpu_workload(name, args, rank, device, barrier, max_over_ranks, with_e2e
     frame_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = max_over_ranks(sum(frame_ms))
     res = {"n": sc.n, "n_grid": sc.n_grid, "frame_ms": frame_ms, "t_ms": t_ms, "clocks": clk.summary(),
-           "active_nodes": active_nodes, "steps": steps}
+           "active_nodes": active_nodes, "steps": steps, "tuning": tuning}
 
     if with_e2e:
         # end to end through the C ABI with host buffers
@@ -224,6 +229,10 @@ def run_batched(args, rank, device, barrier, max_over_ranks, steps=6, loop_steps
     sim.load_batch([sc.x for sc in envs], [sc.particle_volume for sc in envs])
     for i, sc in enumerate(envs):
         sim.set_env_tool(i, 0, sc.tools[0].pose(-1), sc.tools[0].shape)
+    tuning = None
+    if not args.no_autotune:
+        best, times = sim.autotune(S)
+        tuning = {"config": best, "name": mpm.KERNEL_CONFIG_NAMES[best], "ms_per_step_by_config": times}
     s_next = [0]
 
     def set_tools():
@@ -291,7 +300,7 @@ def run_batched(args, rank, device, barrier, max_over_ranks, steps=6, loop_steps
             "env_steps_per_s": env_steps, "particle_steps_per_s": total * S * steps * world / (t_batched / 1e3),
             "ms_per_step": t_batched / steps, "loop_env_steps_per_s": loop_env_steps,
             "loop_ms_per_step": t_loop / loop_steps, "speedup_vs_loop": env_steps / loop_env_steps,
-            "gpu_launches_per_step": S}
+            "gpu_launches_per_step": S, "tuning": tuning}
 
 
 def run_differentiable(args, rank, device, barrier, max_over_ranks, reps=2):
@@ -453,7 +462,7 @@ def main():
     if not args.no_secondary and args.workload != "slab30k":
         r2 = run_gpu_workload("slab30k", args, rank, device, barrier, max_over_ranks, with_e2e=True,
                               steps=max(args.steps, 20))
-        second = {"workload": "slab30k", "n_particles": r2["n"], "n_grid": r2["n_grid"],
+        second = {"workload": "slab30k", "n_particles": r2["n"], "n_grid": r2["n_grid"], "tuning": r2["tuning"],
                   "value": r2["n"] * S * r2["steps"] * world / (r2["t_ms"] / 1e3),
                   "ms_per_step": r2["t_ms"] / r2["steps"],
                   "e2e": r2["n"] * S * r2["steps"] * world / (r2["t_e2e_ms"] / 1e3)}
@@ -503,7 +512,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "n_particles": main_res["n"], "n_grid": main_res["n_grid"],
                    "substeps_per_step": S, "pipeline": args.pipeline, "parallelism": "replicas%d" % world,
-                   "l2": "flushed between timed steps (256 MB write)"},
+                   "l2": "flushed between timed steps (256 MB write)", "kernel_tuning": main_res["tuning"]},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "particle-steps/s", "h2d_bytes_per_step": main_res["h2d"],

@@ -221,6 +221,40 @@ mpm_status mpm_grid_velocity(mpm_handle *h, float *v, int on_device);
  * Host arrays of n entries.  Synchronises. */
 mpm_status mpm_read_order(mpm_handle *h, uint32_t *ids, uint32_t *keys);
 
+/* ------------------------------------------------------------ kernel tuning */
+
+/* Configurations of the fused sub-step kernel: CTA size x passes of particles
+ * staged per shared-memory P2G flush.  More, smaller CTAs waste fewer threads
+ * on sparsely filled grid blocks (small or batched scenes); larger CTAs and
+ * groups amortise the per-block work on dense blocks.  Not in the paper (its
+ * Taichi kernels are tuned by Taichi); a utility of this library. */
+enum {
+    MPM_KERNEL_T256_G2 = 0, /* 256 threads, 512 particles per flush (the default) */
+    MPM_KERNEL_T256_G1 = 1, /* 256 threads, 256 particles per flush */
+    MPM_KERNEL_T128_G2 = 2, /* 128 threads, 256 particles per flush */
+    MPM_KERNEL_T128_G1 = 3, /* 128 threads, 128 particles per flush */
+    MPM_KERNEL_CONFIGS = 4
+};
+
+/* Select the fused kernel configuration (fused pipeline; the split pipeline
+ * ignores it).  MPM_ERR_ARG if out of range or not resident on this GPU. */
+mpm_status mpm_set_kernel_config(mpm_handle *h, int32_t config);
+
+/* The current configuration, its CTA size and the persistent grid size (CTAs
+ * per launch); any output may be NULL. */
+mpm_status mpm_get_kernel_config(mpm_handle *h, int32_t *config, int32_t *threads, int32_t *ctas);
+
+/* Autotuner: time every configuration on the handle's own state (one
+ * untimed call of n_substeps sub-steps, then one timed call, each trial
+ * starting from the same snapshot of the particles and tools), select the
+ * fastest and restore the state as it was (particle order inside the
+ * library may change; mpm_read_particles returns the same values).
+ * times_ms (MPM_KERNEL_CONFIGS floats, -1 for configurations that do not fit)
+ * and best may be NULL.  Needs a loaded fused-pipeline handle
+ * (MPM_ERR_STATE).  Synchronises; allocates a snapshot of 24 floats per
+ * particle, kept by the handle. */
+mpm_status mpm_autotune(mpm_handle *h, int32_t n_substeps, float *times_ms, int32_t *best);
+
 /* -------------------------------------------------- differentiable rollout */
 
 /* Record a rollout of n_substeps sub-steps for mpm_tape_backward: sub-step k

@@ -101,6 +101,7 @@ struct mpm_handle {
     void *alloc_ctx = nullptr;
     std::vector<Alloc> allocs;
     int device = 0, num_sms = 0, fused_grid = 0, elem_grid = 0;
+    int kernel_config = 0;          // MPM_KERNEL_* of the fused sub-step
     int n_envs = 1;
     int sub_chunk = 512;        // sub-steps per captured graph / frame upload
     int tstride = 0;            // tool frames per environment in the uploaded table
@@ -327,7 +328,7 @@ mpm_status issue_substeps(mpm_handle *h, int nsub, bool write_vc_last, cudaStrea
         const ToolFrame *fr = h->d_frames + (size_t)k * h->n_envs * h->tstride;
         const bool vc = write_vc_last && k == nsub - 1;
         if (is_fused(h)) {
-            launch_fused_step(P, h->fb, fr, vc, h->fused_grid, st);
+            launch_fused_step(P, h->fb, fr, vc, h->fused_grid, h->kernel_config, st);
         } else {
             CK(cudaMemsetAsync(h->fb.G[0], 0, sizeof(float4) * (size_t)h->P.n * h->P.n * h->P.n, st));
             launch_p2g_scatter(P, h->fb.P[0], h->fb.vc, n, h->fb.G[0], h->fb.ctrl, h->elem_grid, st);
@@ -341,8 +342,8 @@ mpm_status issue_substeps(mpm_handle *h, int nsub, bool write_vc_last, cudaStrea
 
 mpm_status run_chunk(mpm_handle *h, int nsub, bool write_vc_last) {
     if (!h->use_graphs) return issue_substeps(h, nsub, write_vc_last, h->stream);
-    // graphs are keyed by length, the vc flag and the tool-frame stride
-    const std::pair<int, int> key(nsub, (write_vc_last ? 1 : 0) | (h->tstride << 1));
+    // graphs are keyed by length, the vc flag, the tool-frame stride and the kernel configuration
+    const std::pair<int, int> key(nsub, (write_vc_last ? 1 : 0) | (h->tstride << 1) | (h->kernel_config << 8));
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         cudaGraph_t g = nullptr;
@@ -455,10 +456,10 @@ mpm_status mpm_create(const mpm_config *cfg, void *cuda_stream, mpm_alloc_fn all
     const size_t nn = (size_t)n * n * n * n_envs;   // grid nodes over all environments
     h->nbe = P.nbe;
     h->nblocks = P.nbe * (uint32_t)n_envs;
-    h->chunk_cap = h->nblocks + (uint32_t)(N / kFusedThreads) + 1;
+    h->chunk_cap = h->nblocks + (uint32_t)(N / kFusedMinThreads) + 1;
     h->fb.nblocks = h->nblocks;
     h->elem_grid = h->num_sms * 8;
-    const int occ = fused_step_occupancy(kFusedThreads);
+    const int occ = fused_step_occupancy(h->kernel_config);
     h->fused_grid = h->num_sms * std::max(occ, 1);
 
     mpm_status st;
@@ -1131,6 +1132,105 @@ mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_b
                 for (int i = 0; i < 6; ++i) grad_poses[((size_t)k * nt + t) * 6 + i] += g[6 + i];
             }
     }
+    return MPM_OK;
+}
+
+}  // extern "C"
+
+// =========================================================== kernel tuning
+
+namespace {
+
+mpm_status apply_kernel_config(mpm_handle *h, int config) {
+    const int occ = fused_step_occupancy(config);
+    CK(cudaGetLastError());
+    if (occ < 1) return fail(MPM_ERR_ARG, "kernel configuration %d does not fit on this device", config);
+    h->kernel_config = config;
+    h->fused_grid = h->num_sms * occ;
+    return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpm_status mpm_set_kernel_config(mpm_handle *h, int32_t config) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (config < 0 || config >= kFusedConfigs) return fail(MPM_ERR_ARG, "kernel configuration %d out of range", config);
+    return apply_kernel_config(h, config);
+}
+
+mpm_status mpm_get_kernel_config(mpm_handle *h, int32_t *config, int32_t *threads, int32_t *ctas) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (config) *config = h->kernel_config;
+    if (threads) *threads = fused_step_threads(h->kernel_config);
+    if (ctas) *ctas = h->fused_grid;
+    return MPM_OK;
+}
+
+mpm_status mpm_autotune(mpm_handle *h, int32_t n_substeps, float *times_ms, int32_t *best) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (!is_fused(h)) return fail(MPM_ERR_STATE, "mpm_autotune tunes the fused pipeline");
+    if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
+    if (n_substeps < 1) return fail(MPM_ERR_ARG, "n_substeps must be >= 1");
+    if ((st = poll_error(h, true)) != MPM_OK) return st;
+    if (times_ms)
+        for (int c = 0; c < kFusedConfigs; ++c) times_ms[c] = -1.f;
+    if (h->n == 0) {
+        if (best) *best = h->kernel_config;
+        return MPM_OK;
+    }
+    // snapshot of the state, the tools and the counters; every trial starts from it
+    const size_t n = (size_t)h->n;
+    float *snap = nullptr;
+    if ((st = dalloc_t(h, &snap, 24 * n)) != MPM_OK) return st;   // kept by the handle until destroy
+    float *sx = snap, *sv = snap + 3 * n, *sF = snap + 6 * n, *sC = snap + 15 * n;
+    if ((st = mpm_read_particles(h, sx, sv, sF, sC, 1)) != MPM_OK) return st;
+    const std::vector<HostTool> tools0 = h->tools;
+    const int64_t taken0 = h->taken;
+    std::vector<int64_t> counts(h->n_envs);
+    std::vector<float> vols(h->n_envs);
+    for (int e = 0; e < h->n_envs; ++e) {
+        counts[e] = (int64_t)h->env_off[e + 1] - (int64_t)h->env_off[e];
+        vols[e] = (float)h->env_vol[e];
+    }
+    const int start = h->kernel_config;
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    auto restore = [&]() -> mpm_status {
+        h->tools = tools0;
+        return load_impl(h, counts.data(), sx, sv, sF, sC, vols.data(), 1);
+    };
+    int pick = start;
+    float best_ms = 3.0e38f;
+    for (int c = 0; c < kFusedConfigs && st == MPM_OK; ++c) {
+        if (fused_step_occupancy(c) < 1) continue;
+        if ((st = apply_kernel_config(h, c)) != MPM_OK) break;
+        if ((st = restore()) != MPM_OK) break;
+        if ((st = mpm_step(h, n_substeps)) != MPM_OK) break;      // captures the graphs
+        h->tools = tools0;
+        cudaEventRecord(a, h->stream);
+        if ((st = mpm_step(h, n_substeps)) != MPM_OK) break;
+        cudaEventRecord(b, h->stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) { st = fail(MPM_ERR_CUDA, "cudaEventSynchronize failed"); break; }
+        if ((st = poll_error(h, true)) != MPM_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (times_ms) times_ms[c] = ms;
+        if (ms < best_ms) { best_ms = ms; pick = c; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    mpm_status st2 = apply_kernel_config(h, st == MPM_OK ? pick : start);
+    if (st2 == MPM_OK) st2 = restore();
+    h->taken = taken0;
+    if (st != MPM_OK) return st;
+    if (st2 != MPM_OK) return st2;
+    if (best) *best = pick;
     return MPM_OK;
 }
 

@@ -39,17 +39,19 @@ namespace gbmpm {
 
 namespace {
 
-constexpr int T = kFusedThreads;
-constexpr int NW = T / 32;
 constexpr int CMAX = 512;      // run candidates (source chunk x direction) per block
-constexpr int GROUP = 2 * T;   // particles staged per arena flush
 constexpr float kFix = 4194304.0f;      // 2^22
 constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23: float -> nearest int for |v| < 2^22
 // arena node (x, y, z) in [0,8)^3 sits at x + kAy y + kAz z: kAz = 68 keeps the
 // bases of a z-pair of cells in distinct shared-memory banks
 constexpr int kAy = 8, kAz = 68, kArena = 8 * kAz;
 
+// Shared memory of a CTA of T threads that stages GP passes (GP T particles)
+// per arena flush.
+template <int T, int GP>
 struct FusedSmem {
+    static constexpr int NW = T / 32;
+    static constexpr int GROUP = GP * T;
     // double-buffered per-block inputs, prefetched with cp.async one block ahead:
     // the 6^3 grid nodes [4b, 4b+5]^3 (mass, momentum; turned into velocities
     // in place by the grid operation) and the block's inbox of incoming runs
@@ -75,8 +77,13 @@ struct FusedSmem {
     uint32_t ncand, total, out_base, chunk_first, npass, mask, bmax;
 };
 
-// three CTAs per SM: 228 KB of shared memory per SM, 1 KB reserved per CTA
-static_assert(3 * (sizeof(FusedSmem) + 1024) <= 228 * 1024, "shared memory for three CTAs per SM");
+// resident CTAs per SM for which a configuration is compiled: 228 KB of shared
+// memory per SM with 1 KB reserved per CTA, 64 K registers
+template <int T, int GP>
+constexpr int kMinBlocks = T == 256 ? 3 : (GP == 1 ? 5 : 4);
+static_assert(3 * (sizeof(FusedSmem<256, 2>) + 1024) <= 228 * 1024, "shared memory for three CTAs per SM");
+static_assert(4 * (sizeof(FusedSmem<128, 2>) + 1024) <= 228 * 1024, "shared memory for four CTAs per SM");
+static_assert(5 * (sizeof(FusedSmem<128, 1>) + 1024) <= 228 * 1024, "shared memory for five CTAs per SM");
 
 __device__ __forceinline__ int dir_dx(int d) { return d % 3 - 1; }
 __device__ __forceinline__ int dir_dy(int d) { return (d / 3) % 3 - 1; }
@@ -106,7 +113,8 @@ __device__ __forceinline__ void cp_async_wait_but_one() { asm volatile("cp.async
 
 // Slot of logical index j among the block's incoming runs (binary search of
 // the runs' exclusive prefix).
-__device__ __forceinline__ uint32_t source_slot(const FusedSmem &s, uint32_t ncand, uint32_t j) {
+template <class Smem>
+__device__ __forceinline__ uint32_t source_slot(const Smem &s, uint32_t ncand, uint32_t j) {
     int lo = 0, hi = (int)ncand - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -116,7 +124,8 @@ __device__ __forceinline__ uint32_t source_slot(const FusedSmem &s, uint32_t nca
 }
 
 // Start copying the particle with logical index j into this thread's slot.
-__device__ __forceinline__ void prefetch_particle(FusedSmem &s, const PState &in, uint32_t ncand, uint32_t j, int tid) {
+template <class Smem>
+__device__ __forceinline__ void prefetch_particle(Smem &s, const PState &in, uint32_t ncand, uint32_t j, int tid) {
     const uint32_t src = source_slot(s, ncand, j);
     cp_async16(&s.pxi[tid], &in.xi[src], true);
     cp_async16(&s.pf0[tid], &in.f0[src], true);
@@ -126,7 +135,8 @@ __device__ __forceinline__ void prefetch_particle(FusedSmem &s, const PState &in
 
 // Start copying global block b's grid region of G_k, its inbox, and its
 // environment's material and tool frames into buffer buf.
-__device__ __forceinline__ void prefetch_block(FusedSmem &s, int buf, uint32_t b, const uint4 *__restrict__ inbox_in,
+template <int T, class Smem>
+__device__ __forceinline__ void prefetch_block(Smem &s, int buf, uint32_t b, const uint4 *__restrict__ inbox_in,
                                                const float4 *__restrict__ Gcur, const DevParams &P,
                                                const ToolFrame *__restrict__ tools, int tid) {
     const uint32_t e = b / P.nbe, bl = b % P.nbe;
@@ -156,10 +166,13 @@ __device__ __forceinline__ void prefetch_block(FusedSmem &s, int buf, uint32_t b
 }
 
 
-template <bool WRITE_VC>
-__global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, const ToolFrame *__restrict__ tools) {
+template <bool WRITE_VC, int T, int GP>
+__global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P, FusedBufs B,
+                                                                     const ToolFrame *__restrict__ tools) {
+    using Smem = FusedSmem<T, GP>;
+    constexpr int NW = Smem::NW, GROUP = Smem::GROUP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    FusedSmem &s = *reinterpret_cast<FusedSmem *>(smem_raw);
+    Smem &s = *reinterpret_cast<Smem *>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Ctrl *ctrl = B.ctrl;
     const uint32_t step = *(volatile uint32_t *)&ctrl->step;
@@ -191,14 +204,15 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
     for (uint32_t q = blockIdx.x * T + tid; q < nclr * 64u; q += gridDim.x * T)
         Gclr[clr[q >> 6] * 64u + (q & 63u)] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    // prologue: first work item and its inputs
+    // prologue: work item blockIdx.x first (the shared counter hands out items
+    // gridDim.x, gridDim.x + 1, ... afterwards) and its inputs
     if (tid == T - 1) {
-        const uint32_t it = atomicAdd(&ctrl->work, 1u);
+        const uint32_t it = blockIdx.x;
         s.items[0] = it;
         s.bids[0] = it < nact ? act[it] : 0u;
     }
     __syncthreads();
-    if (s.items[0] < nact) prefetch_block(s, 0, s.bids[0], inbox_in, Gcur, P, tools, tid);
+    if (s.items[0] < nact) prefetch_block<T>(s, 0, s.bids[0], inbox_in, Gcur, P, tools, tid);
     cp_async_wait_all();
     __syncthreads();
 
@@ -213,15 +227,14 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
         const float m = ep.mass;
         // the next work item, fetched while this block is set up
         if (tid == T - 1) {
-            const uint32_t it = atomicAdd(&ctrl->work, 1u);
+            const uint32_t it = gridDim.x + atomicAdd(&ctrl->work, 1u);
             s.items[cb ^ 1] = it;
             s.bids[cb ^ 1] = it < nact ? act[it] : 0u;
         }
         float4 *gv = s.graw[cb];
 
-        // 1. grid operation of the 6^3 G2P region, in place (warps 1-7)
-        if (tid >= 32 && tid < 32 + 216) {
-            const int q = tid - 32;
+        // 1. grid operation of the 6^3 G2P region, in place (warps 1 ..)
+        for (int q = tid - 32; q >= 0 && q < 216; q += T - 32) {
             const int i = 4 * bx + q % 6, j = 4 * by + (q / 6) % 6, k = 4 * bz + q / 36;
             const float4 g = gv[q];
             float3 v = make_float3(0.f, 0.f, 0.f);
@@ -328,14 +341,14 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
         // both land while this block computes
         if (npass > 0 && (uint32_t)tid < total) prefetch_particle(s, in, ncand, (uint32_t)tid, tid);
         cp_async_commit();
-        if (s.items[cb ^ 1] < nact) prefetch_block(s, cb ^ 1, s.bids[cb ^ 1], inbox_in, Gcur, P, tools, tid);
+        if (s.items[cb ^ 1] < nact) prefetch_block<T>(s, cb ^ 1, s.bids[cb ^ 1], inbox_in, Gcur, P, tools, tid);
         else cp_async_commit();
         const int ox = 4 * bx - 1, oy = 4 * by - 1, oz = 4 * bz - 1;   // arena origin
 
         for (uint32_t pass = 0; pass < npass; ++pass) {
             const uint32_t j = pass * T + tid;
             const bool valid = j < total;
-            const int slot = (pass & 1) * T + tid;     // staging slot within the group
+            const int slot = (pass % GP) * T + tid;    // staging slot within the group
             int d = 31;
             float nxp = 0.f, nyp = 0.f, nzp = 0.f, idf = 0.f, Fn[9], Cm[9], vx = 0.f, vy = 0.f, vz = 0.f;
             // this pass's particle is in the slot; the next block's inputs may still be landing
@@ -519,11 +532,11 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
                 if (WRITE_VC) store_vc(B.vc, pos, vx, vy, vz, Cm);
             }
 
-            // --- P2G of the staged group (after every second pass and the last one).
+            // --- P2G of the staged group (after every GP-th pass and the last one).
             // Lane l of warp w scatters staged slot 2 l + (w & 1) + 64 (w >> 1):
             // neighbouring lanes then hold particles of different cells.
-            if ((pass & 1) == 1 || pass + 1 == npass) {
-                const int nstaged = (int)min((uint32_t)GROUP, total - (pass & ~1u) * T);
+            if (pass % GP == GP - 1 || pass + 1 == npass) {
+                const int nstaged = (int)min((uint32_t)GROUP, total - (pass - pass % GP) * T);
                 const float bmax = __uint_as_float(s.bmax);
                 const float sv = bmax > 0.f ? kFix / bmax : 1.0f;   // momentum fixed-point scale
                 for (int q0 = tid; q0 < GROUP; q0 += T) {
@@ -535,10 +548,11 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
                     bspline_weights(s.st_f[0][q], wx);
                     bspline_weights(s.st_f[1][q], wy);
                     bspline_weights(s.st_f[2][q], wz);
+                    // momentum inputs in fixed-point units
                     float A[9];
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) A[c] = s.st_a[c][q];
-                    const float qx = s.st_q[0][q], qy = s.st_q[1][q], qz = s.st_q[2][q];
+                    for (int c = 0; c < 9; ++c) A[c] = s.st_a[c][q] * sv;
+                    const float qx = s.st_q[0][q] * sv, qy = s.st_q[1][q] * sv, qz = s.st_q[2][q] * sv;
 #pragma unroll
                     for (int kk = 0; kk < 3; ++kk) {
 #pragma unroll
@@ -549,12 +563,12 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
                             const float rz = qz + A[7] * jj + A[8] * kk;
 #pragma unroll
                             for (int ii = 0; ii < 3; ++ii) {
-                                const float w = wx[ii] * wjk, ws = w * sv;
+                                const float w = wx[ii] * wjk;
                                 const int a = base + ii + kAy * jj + kAz * kk;
                                 atomicAdd(&s.acc[0][a], fix_round(fmaf(w, kFix, kMagic)));
-                                atomicAdd(&s.acc[1][a], fix_round(fmaf(ws, rx + A[0] * ii, kMagic)));
-                                atomicAdd(&s.acc[2][a], fix_round(fmaf(ws, ry + A[3] * ii, kMagic)));
-                                atomicAdd(&s.acc[3][a], fix_round(fmaf(ws, rz + A[6] * ii, kMagic)));
+                                atomicAdd(&s.acc[1][a], fix_round(fmaf(w, rx + A[0] * ii, kMagic)));
+                                atomicAdd(&s.acc[2][a], fix_round(fmaf(w, ry + A[3] * ii, kMagic)));
+                                atomicAdd(&s.acc[3][a], fix_round(fmaf(w, rz + A[6] * ii, kMagic)));
                             }
                         }
                     }
@@ -617,30 +631,49 @@ __global__ void __launch_bounds__(T, 3) k_fused_step(DevParams P, FusedBufs B, c
     }
 }
 
-template <bool V>
-void set_smem_attr() {
-    cudaFuncSetAttribute(k_fused_step<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FusedSmem));
+template <int T, int GP>
+void launch_variant(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, bool write_vc, int grid,
+                    cudaStream_t st) {
+    if (write_vc)
+        k_fused_step<true, T, GP><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools);
+    else
+        k_fused_step<false, T, GP><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools);
+}
+
+template <int T, int GP>
+int variant_occupancy() {
+    const int bytes = (int)sizeof(FusedSmem<T, GP>);
+    cudaFuncSetAttribute(k_fused_step<true, T, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_fused_step<false, T, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fused_step<true, T, GP>, T, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_step<false, T, GP>, T, bytes);
+    return a < b ? a : b;
 }
 
 }  // namespace
 
 void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, bool write_vc, int grid,
-                       cudaStream_t st) {
-    if (write_vc)
-        k_fused_step<true><<<grid, T, sizeof(FusedSmem), st>>>(P, B, tools);
-    else
-        k_fused_step<false><<<grid, T, sizeof(FusedSmem), st>>>(P, B, tools);
+                       int config, cudaStream_t st) {
+    switch (config) {
+    case 1: launch_variant<256, 1>(P, B, tools, write_vc, grid, st); break;
+    case 2: launch_variant<128, 2>(P, B, tools, write_vc, grid, st); break;
+    case 3: launch_variant<128, 1>(P, B, tools, write_vc, grid, st); break;
+    default: launch_variant<256, 2>(P, B, tools, write_vc, grid, st); break;
+    }
 }
+
+int fused_step_threads(int config) { return config >= 2 ? 128 : 256; }
 
 // Also opts the kernel into its dynamic shared memory size on the current
 // device; called when a handle is created.
-int fused_step_occupancy(int threads) {
-    set_smem_attr<true>();
-    set_smem_attr<false>();
-    int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fused_step<true>, threads, sizeof(FusedSmem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_step<false>, threads, sizeof(FusedSmem));
-    return a < b ? a : b;
+int fused_step_occupancy(int config) {
+    switch (config) {
+    case 1: return variant_occupancy<256, 1>();
+    case 2: return variant_occupancy<128, 2>();
+    case 3: return variant_occupancy<128, 1>();
+    default: return variant_occupancy<256, 2>();
+    }
 }
 
 }  // namespace gbmpm

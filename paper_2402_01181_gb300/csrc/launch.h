@@ -84,10 +84,14 @@ struct FusedBufs {
     Ctrl *ctrl;
     uint32_t nblocks;
 };
+// config (MPM_KERNEL_*): 0 = 256 threads, 2 passes per P2G flush; 1 = 256, 1;
+// 2 = 128, 2; 3 = 128, 1
 void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, bool write_vc, int grid,
-                       cudaStream_t st);
-int fused_step_occupancy(int threads);
-constexpr int kFusedThreads = 256;
+                       int config, cudaStream_t st);
+int fused_step_occupancy(int config);
+int fused_step_threads(int config);
+constexpr int kFusedConfigs = 4;
+constexpr int kFusedMinThreads = 128;     // chunk tables are sized for the smallest CTA
 // Inbox of a block: entry d * kNpMax + p holds the run of source pass p
 // coming from direction d (source block = block - dir(d)); the last entry,
 // stamped, says that some source had more than kNpMax passes.

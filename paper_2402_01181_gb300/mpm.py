@@ -35,6 +35,9 @@ MPM_TOOL_CAPSULE = 0
 MPM_TOOL_BOX = 1
 MPM_TOOL_SAMPLED = 2
 MPM_MAX_FIELDS = 16
+MPM_KERNEL_CONFIGS = 4
+KERNEL_CONFIG_NAMES = {0: "256 threads, 2 passes per flush", 1: "256 threads, 1 pass per flush",
+                       2: "128 threads, 2 passes per flush", 3: "128 threads, 1 pass per flush"}
 MPM_MAX_FIELD_RES = 1024
 
 STATUS_NAMES = {0: "MPM_OK", -1: "MPM_ERR_ARG", -2: "MPM_ERR_ALLOC", -3: "MPM_ERR_CUDA", -4: "MPM_ERR_NUMERIC",
@@ -84,6 +87,10 @@ SIGNATURES = [
     ("mpm_add_sampled_field", ct.c_int, [ct.c_void_p, ct.c_int32, _DP, ct.c_double, ct.c_void_p, ct.c_int,
                                          ct.POINTER(ct.c_int32)]),
     ("mpm_tape_record", ct.c_int, [ct.c_void_p, ct.c_int32, _DP, ct.c_int32]),
+    ("mpm_set_kernel_config", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("mpm_get_kernel_config", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
+                                         ct.POINTER(ct.c_int32)]),
+    ("mpm_autotune", ct.c_int, [ct.c_void_p, ct.c_int32, _FP, ct.POINTER(ct.c_int32)]),
     ("mpm_tape_backward", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
                                      _DP, _DP, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
 ]
@@ -124,6 +131,9 @@ mpm_read_order = lib.mpm_read_order
 mpm_block_sort_noalloc = lib.mpm_block_sort_noalloc
 mpm_add_sampled_field = lib.mpm_add_sampled_field
 mpm_tape_record = lib.mpm_tape_record
+mpm_set_kernel_config = lib.mpm_set_kernel_config
+mpm_get_kernel_config = lib.mpm_get_kernel_config
+mpm_autotune = lib.mpm_autotune
 mpm_tape_backward = lib.mpm_tape_backward
 
 
@@ -283,6 +293,22 @@ class Sim:
         p = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(6))
         s = self._shape_for(shape, field)
         check(mpm_set_tool_pose(self.h, int(tool_id), p.ctypes.data_as(_DP), s.ctypes.data_as(_FP)))
+
+    def set_kernel_config(self, config):
+        check(mpm_set_kernel_config(self.h, int(config)))
+
+    def kernel_config(self):
+        c, t, g = ct.c_int32(), ct.c_int32(), ct.c_int32()
+        check(mpm_get_kernel_config(self.h, ct.byref(c), ct.byref(t), ct.byref(g)))
+        return {"config": c.value, "threads": t.value, "ctas": g.value}
+
+    def autotune(self, n_substeps=25):
+        """Time every fused-kernel configuration on this state, keep the
+        fastest; returns (best, times in ms per configuration)."""
+        times = (ct.c_float * MPM_KERNEL_CONFIGS)()
+        best = ct.c_int32()
+        check(mpm_autotune(self.h, int(n_substeps), times, ct.byref(best)))
+        return best.value, [float(t) for t in times]
 
     def tape_record(self, poses, checkpoint_every=50):
         """Record a rollout of len(poses) sub-steps, poses (K, n_tools, 6):

@@ -60,5 +60,8 @@ def test_argument_validation_without_gpu(lib):
     fid = ct.c_int32(-1)
     o = (ct.c_double * 3)()
     assert lib.mpm_add_sampled_field(None, 4, o, 0.1, None, 0, ct.byref(fid)) == lib.MPM_ERR_ARG
+    assert lib.mpm_set_kernel_config(None, 0) == lib.MPM_ERR_ARG
+    assert lib.mpm_autotune(None, 1, None, None) == lib.MPM_ERR_ARG
+    assert lib.mpm_tape_record(None, 1, None, 1) == lib.MPM_ERR_ARG
     assert lib.mpm_destroy(None) == lib.MPM_ERR_ARG
     assert lib.mpm_read_particles(None, None, None, None, None, 0) == lib.MPM_ERR_ARG
