@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true", help="skip the 30K slab line")
     ap.add_argument("--no-differentiable", action="store_true", help="skip the differentiable-rollout line")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default fused-kernel configuration")
+    ap.add_argument("--kernel-config", type=int, default=None,
+                    help="fused-kernel configuration to use instead of autotuning (MPM_KERNEL_*)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-environment measurement")
     ap.add_argument("--batch-envs", type=int, default=256)
@@ -152,7 +154,11 @@ def run_gpu_workload(name, args, rank, device, barrier, max_over_ranks, with_e2e
     tool_frames = [(t, tool) for t, tool in enumerate(sc.tools)]
     s_next = [0]
     tuning = None
-    if pipe == mpm.MPM_PIPELINE_FUSED and not args.no_autotune:
+    if pipe == mpm.MPM_PIPELINE_FUSED and args.kernel_config is not None:
+        sim.set_kernel_config(args.kernel_config)
+        tuning = {"config": args.kernel_config, "name": mpm.KERNEL_CONFIG_NAMES[args.kernel_config],
+                  "ms_per_step_by_config": None}
+    elif pipe == mpm.MPM_PIPELINE_FUSED and not args.no_autotune:
         best, times = sim.autotune(S)          # restores the state it starts from
         tuning = {"config": best, "name": mpm.KERNEL_CONFIG_NAMES[best], "ms_per_step_by_config": times}
 
@@ -489,17 +495,39 @@ def main():
     launch_ms = main_res["t_ms"] / (args.steps * S)      # per fused launch (frame time / sub-steps)
     achieved = bpp * main_res["n"] / (launch_ms / 1e3) / 1e9
     traffic = None
+    counts = None
     try:
         with open(TRAFFIC_FILE) as fh:
             tr = json.load(fh)
-        if tr.get("kernel_sha") == kernel_source_sha() and tr.get("workload") == args.workload:
-            traffic = tr.get("bytes_per_launch")
+        rec = tr.get("configs", {}).get(str((main_res["tuning"] or {}).get("config", 0)))
+        if tr.get("kernel_sha") == kernel_source_sha() and tr.get("workload") == args.workload and rec:
+            traffic = rec.get("bytes_per_launch")
+            counts = rec
     except Exception:
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_fused_step" if args.pipeline == "fused"
                 else "p2g+grid+g2p", "algorithmic_bytes_per_particle_step": bpp,
                 "launch_us": launch_ms * 1e3}
+    # the CUDA-core side: FP32 FLOPs and thread instructions per particle-step
+    # from the ncu capture of this kernel, against the rates of this GPU at the
+    # sampled maximum SM clock (128 FP32 lanes and 4 x 32 issue lanes per SM)
+    alu = None
+    if counts is not None:
+        import torch
+        sms = torch.cuda.get_device_properties(device).multi_processor_count
+        mhz = main_res["clocks"].get("sm_max_mhz") or 2070.0
+        per_s = main_res["n"] / (launch_ms / 1e3)
+        flops = counts["fp32_flop_per_particle_step"] * per_s
+        insts = counts["thread_inst_per_particle_step"] * per_s
+        fpeak = sms * 128 * 2 * mhz * 1e6
+        ipeak = sms * 4 * 32 * mhz * 1e6
+        alu = {"bound": "alu", "achieved": flops / 1e12, "peak": fpeak / 1e12, "unit": "TFLOP/s",
+               "frac": flops / fpeak, "issue": {"achieved": insts / 1e12, "peak": ipeak / 1e12,
+                                                "unit": "T thread-instructions/s", "frac": insts / ipeak},
+               "per_particle_step": {"fp32_flop": counts["fp32_flop_per_particle_step"],
+                                     "thread_inst": counts["thread_inst_per_particle_step"]},
+               "peak_kind": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (sms, mhz)}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, sample = time_oracle(args.workload, 15.0)
@@ -514,6 +542,7 @@ def main():
                    "substeps_per_step": S, "pipeline": args.pipeline, "parallelism": "replicas%d" % world,
                    "l2": "flushed between timed steps (256 MB write)", "kernel_tuning": main_res["tuning"]},
         "roofline": roofline,
+        "alu_roofline": alu,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "particle-steps/s", "h2d_bytes_per_step": main_res["h2d"],
                 "d2h_bytes_per_step": main_res["d2h"]},

@@ -63,6 +63,12 @@ struct FusedSmem {
     int acc[4][kArena];            // P2G arena over nodes [4b-1, 4b+6]^3 (fixed point, padded strides)
     // staged P2G inputs of one group: packed arena base, fx (3), q (3), A dx (9)
     int st_base[GROUP];
+    // the group's particles bucketed by the shared-memory bank of their arena
+    // base: rank within the bucket (and the bucket) per slot, bucket sizes, and
+    // the slots in bucket order
+    uint16_t st_key[GROUP];
+    uint16_t order[GROUP];
+    uint32_t ccount[32];
     float st_f[3][GROUP];
     float st_q[3][GROUP];
     float st_a[9][GROUP];
@@ -242,6 +248,7 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
             gv[q] = make_float4(v.x, v.y, v.z, 0.f);
         }
         for (int q = tid; q < 4 * kArena; q += T) (&s.acc[0][0])[q] = 0;
+        if (tid < 32) s.ccount[tid] = 0u;
         for (int q = tid; q < 2 * NW * 28; q += T) (&s.wcnt[0][0][0])[q] = 0u;
         // 2. warp 0: the runs heading to b, in ascending source-block order
         //    (direction d = 26 .. 0, source pass 0 .. 3), with their exclusive
@@ -434,7 +441,10 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
                 const int ax0 = hx - ox, ay0 = hy - oy, az0 = hz - oz;
                 const bool in_arena = ax0 >= 0 && ax0 <= 5 && ay0 >= 0 && ay0 <= 5 && az0 >= 0 && az0 <= 5;
                 if (in_arena) {
-                    s.st_base[slot] = ax0 + kAy * ay0 + kAz * az0;
+                    const int abase = ax0 + kAy * ay0 + kAz * az0;
+                    s.st_base[slot] = abase;
+                    const uint32_t cls = (uint32_t)abase & 31u;
+                    s.st_key[slot] = (uint16_t)(cls | (atomicAdd(&s.ccount[cls], 1u) << 5));
                     s.st_f[0][slot] = ex; s.st_f[1][slot] = ey; s.st_f[2][slot] = ez;
                     s.st_q[0][slot] = qx; s.st_q[1][slot] = qy; s.st_q[2][slot] = qz;
 #pragma unroll
@@ -539,9 +549,32 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
                 const int nstaged = (int)min((uint32_t)GROUP, total - (pass - pass % GP) * T);
                 const float bmax = __uint_as_float(s.bmax);
                 const float sv = bmax > 0.f ? kFix / bmax : 1.0f;   // momentum fixed-point scale
-                for (int q0 = tid; q0 < GROUP; q0 += T) {
-                    const int q = (q0 & ~255) + ((q0 & 31) * 2 + ((q0 >> 5) & 1)) + 64 * ((q0 & 255) >> 6);
-                    if (q >= nstaged) continue;
+                // order the group's arena particles by bank bucket (a counting sort over
+                // 32 buckets): lane l of a warp then takes sorted position l * rows + j,
+                // so the lanes of a warp sit in distinct banks at every stencil node
+                const uint32_t cnt = s.ccount[lane];
+                uint32_t cincl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, cincl, o);
+                    if (lane >= o) cincl += y;
+                }
+                const uint32_t nin = __shfl_sync(0xffffffffu, cincl, 31);
+                const uint32_t cexcl = cincl - cnt;
+#pragma unroll
+                for (int p = 0; p < GP; ++p) {
+                    const int sl = p * T + tid;
+                    const bool mine = sl < nstaged && s.st_base[sl] >= 0;
+                    const uint32_t key = mine ? s.st_key[sl] : 0u;
+                    const uint32_t off = __shfl_sync(0xffffffffu, cexcl, key & 31u);
+                    if (mine) s.order[off + (key >> 5)] = (uint16_t)sl;
+                }
+                __syncthreads();
+                const uint32_t rows = (nin + 31u) >> 5;
+                for (uint32_t jr = warp; jr < rows; jr += NW) {
+                    const uint32_t pos = lane * rows + jr;
+                    if (pos >= nin) continue;
+                    const int q = s.order[pos];
                     const int base = s.st_base[q];
                     if (base < 0) continue;
                     float wx[3], wy[3], wz[3];
@@ -588,9 +621,10 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
                         s.acc[0][a] = 0; s.acc[1][a] = 0; s.acc[2][a] = 0; s.acc[3][a] = 0;
                     }
                 }
-                // every thread read s.bmax before the barrier above; the next
-                // group's atomicMax comes after the barrier below
+                // every thread read s.bmax and the bucket sizes before the barriers
+                // above; the next group's atomics come after the barrier below
                 if (tid == 0) s.bmax = 0;
+                if (tid < 32) s.ccount[tid] = 0u;
                 __syncthreads();
             }
         }

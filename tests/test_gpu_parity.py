@@ -203,6 +203,37 @@ def test_block1m_single_step_full_size(M):
     assert mask.sum() <= 10
 
 
+def test_block8m_single_step_full_size(M):
+    """The largest roofline workload (8M particles on a 256^3 grid), autotuned
+    as the benchmark runs its workloads: one 25-sub-step call, the block
+    keys and the order of the per-sub-step sort checked in full, then one
+    more sub-step compared with the oracle for every particle."""
+    sc = scenes.block8m()
+    sim = M.sim_from_scene(sc)
+    tool = sc.tools[0]
+    sim.autotune(25)
+    sim.set_tool(0, tool.pose(24), tool.shape)
+    sim.step(25)
+    state = sim.read()
+    ids, keys = sim.read_order()
+    k_ref = O.block_keys(sc.n_grid, state["x"])
+    assert np.array_equal(np.sort(ids), np.arange(sc.n))
+    assert np.array_equal(keys, k_ref[ids])
+    assert np.all(np.diff(keys.astype(np.int64)) >= 0)
+    sim.set_tool(0, tool.pose(25), tool.shape)
+    sim.step(1)
+    out = sim.read()
+    sim.close()
+    st = H.oracle_state(state)
+    mask = H.contact_mask_nodes(sc, st, 25)
+    skip = H.particles_touching(mask, st.x, sc.n_grid)
+    frames, nt = O.frames_for_steps(sc.tools, 25, 1, sc.dt, 1)
+    O.run(O.OracleParams.from_scene(sc), st, 1, frames, nt)
+    ok, errs = H.compare_particles(out, st, sc.dx, skip)
+    assert ok, errs
+    assert mask.sum() <= 20
+
+
 # --------------------------------------------------------------- sorting
 
 def test_sort_order_is_the_stable_counting_sort(M):
