@@ -930,3 +930,115 @@ int orc_step_adjoint(const orc_params *p, const orc_tool *tools, int32_t ntools,
     free(gm); free(gmv); free(gv); free(gvb); free(gmb); free(gmvb);
     return 0;
 }
+
+/* ======================================================================
+ * Surface extraction (the renderer's Marching Cubes step of Sec. III).
+ *
+ * The iso-surface field >= iso of a node field is triangulated cell by
+ * cell.  Each cell is split into six tetrahedra around its diagonal from
+ * corner 0 to corner 7 (corner c sits at offset (c & 1, (c >> 1) & 1,
+ * (c >> 2) & 1)); every tetrahedron contributes 0, 1 or 2 triangles, and
+ * neighbouring cells split their shared faces alike, so the surface is
+ * closed.  Vertices lie on tetrahedron edges at the linear interpolation
+ * of the field, computed from the lower-numbered corner; triangles face
+ * away from the inside (field >= iso).  This reading avoids the ambiguous
+ * faces of the 256-case cube table.
+ * ====================================================================== */
+
+static const int orc_tet_paths[6][2] = {{1, 3}, {1, 5}, {2, 3}, {2, 6}, {4, 5}, {4, 6}};
+
+static void corner_offset(int c, int *o)
+{
+    o[0] = c & 1; o[1] = (c >> 1) & 1; o[2] = (c >> 2) & 1;
+}
+
+/* sign of det[B - A, C - A, D - A] for cube corners A..D (exact integers) */
+static int tet_orientation(int a, int b, int c, int d)
+{
+    int pa[3], pb[3], pc[3], pd[3];
+    corner_offset(a, pa); corner_offset(b, pb); corner_offset(c, pc); corner_offset(d, pd);
+    const int u[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+    const int v[3] = {pc[0] - pa[0], pc[1] - pa[1], pc[2] - pa[2]};
+    const int w[3] = {pd[0] - pa[0], pd[1] - pa[1], pd[2] - pa[2]};
+    const int det = u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) + u[2] * (v[0] * w[1] - v[1] * w[0]);
+    return det > 0 ? 1 : -1;
+}
+
+/* point where the field crosses iso on the edge between cube corners a, b */
+static void edge_point(const int *cell, int a, int b, const double *f, double iso, double dx, double *out)
+{
+    if (a > b) { const int t = a; a = b; b = t; }
+    int pa[3], pb[3];
+    corner_offset(a, pa);
+    corner_offset(b, pb);
+    const double t = (iso - f[a]) / (f[b] - f[a]);
+    for (int d = 0; d < 3; ++d)
+        out[d] = ((double)(cell[d] + pa[d]) + t * (double)(pb[d] - pa[d])) * dx;
+}
+
+static int64_t emit(double *out, int64_t cnt, int64_t max_tri, const int *cell, const double *f, double iso,
+                    double dx, const int e[3][2])
+{
+    if (cnt < max_tri && out)
+        for (int v = 0; v < 3; ++v) edge_point(cell, e[v][0], e[v][1], f, iso, dx, out + 9 * cnt + 3 * v);
+    return cnt + 1;
+}
+
+/* Triangles of one tetrahedron (corners t[4] positively oriented). */
+static int64_t tet_triangles(const int *cell, const int *t, const double *f, double iso, double dx, double *out,
+                             int64_t cnt, int64_t max_tri)
+{
+    int in[4], nin = 0;
+    for (int q = 0; q < 4; ++q) { in[q] = f[t[q]] >= iso; nin += in[q]; }
+    if (nin == 0 || nin == 4) return cnt;
+    if (nin == 1 || nin == 3) {
+        /* the lone vertex (inside for nin = 1, outside for nin = 3) first, in
+           an even permutation of t */
+        int lone = 0;
+        for (int q = 0; q < 4; ++q) if (in[q] == (nin == 1)) lone = q;
+        static const int even_first[4][4] = {{0, 1, 2, 3}, {1, 0, 3, 2}, {2, 0, 1, 3}, {3, 0, 2, 1}};
+        const int *p = even_first[lone];
+        int e[3][2] = {{t[p[0]], t[p[1]]}, {t[p[0]], t[p[2]]}, {t[p[0]], t[p[3]]}};
+        if (nin == 3) { int s0 = e[1][0], s1 = e[1][1]; e[1][0] = e[2][0]; e[1][1] = e[2][1]; e[2][0] = s0; e[2][1] = s1; }
+        return emit(out, cnt, max_tri, cell, f, iso, dx, e);
+    }
+    /* two inside (p, q) and two outside (r, s), (p, q, r, s) an even permutation */
+    int ins[2], outs[2], a = 0, b = 0;
+    for (int k = 0; k < 4; ++k) { if (in[k]) ins[a++] = k; else outs[b++] = k; }
+    int perm[4] = {ins[0], ins[1], outs[0], outs[1]};
+    int inv = 0;                                  /* parity of perm */
+    for (int i = 0; i < 4; ++i)
+        for (int j = i + 1; j < 4; ++j) inv += perm[i] > perm[j];
+    if (inv & 1) { const int x = perm[2]; perm[2] = perm[3]; perm[3] = x; }
+    const int P = t[perm[0]], Q = t[perm[1]], R = t[perm[2]], S = t[perm[3]];
+    const int e1[3][2] = {{P, R}, {P, S}, {Q, S}};
+    const int e2[3][2] = {{P, R}, {Q, S}, {Q, R}};
+    cnt = emit(out, cnt, max_tri, cell, f, iso, dx, e1);
+    return emit(out, cnt, max_tri, cell, f, iso, dx, e2);
+}
+
+/* field: n^3 node values, [i][j][k] with k fastest; node (i, j, k) sits at
+ * (i, j, k) dx.  Writes up to max_tri triangles (9 doubles each: three
+ * vertices) in cell order (i, j, k) with k fastest, tetrahedra in the order
+ * of orc_tet_paths; returns the total number of triangles. */
+int64_t orc_surface(int32_t n, const double *field, double iso, double dx, double *out, int64_t max_tri)
+{
+    int64_t cnt = 0;
+    for (int i = 0; i + 1 < n; ++i)
+        for (int j = 0; j + 1 < n; ++j)
+            for (int k = 0; k + 1 < n; ++k) {
+                const int cell[3] = {i, j, k};
+                double f[8];
+                for (int c = 0; c < 8; ++c) {
+                    int o[3];
+                    corner_offset(c, o);
+                    f[c] = field[node_index(n, i + o[0], j + o[1], k + o[2])];
+                }
+                for (int q = 0; q < 6; ++q) {
+                    int t[4] = {0, orc_tet_paths[q][0], orc_tet_paths[q][1], 7};
+                    if (tet_orientation(t[0], t[1], t[2], t[3]) < 0) { const int x = t[1]; t[1] = t[2]; t[2] = x; }
+                    cnt = tet_triangles(cell, t, f, iso, dx, out, cnt, max_tri);
+                }
+            }
+    return cnt;
+}

@@ -97,6 +97,8 @@ def lib():
                                            _D, _D]
             L.orc_step_adjoint.restype = ct.c_int
             L.orc_lame_vjp.argtypes = [ct.c_double, ct.c_double, ct.c_double, ct.c_double, _D, _D]
+            L.orc_surface.argtypes = [ct.c_int32, _D, ct.c_double, ct.c_double, _D, ct.c_int64]
+            L.orc_surface.restype = ct.c_int64
             _lib = L
     return _lib
 
@@ -474,3 +476,17 @@ def rollout_loss_and_gradients(prm: OracleParams, st0: State, tools, pose_init, 
                 pose_bar[k - 1, t] += g[:6]
     return {"loss": loss, "E": Eb, "nu": nub, "poses": pose_bar, "state0": bar, "final": final,
             "lame": lame, "frames": fbar}
+
+
+# ----------------------------------------------------------- the surface
+
+def surface(field, iso, dx):
+    """Triangles (T, 3, 3) of the iso-surface field >= iso of an n^3 node
+    field ([i, j, k], node (i, j, k) at (i, j, k) dx), in cell order."""
+    f = np.ascontiguousarray(field, dtype=np.float64)
+    n = f.shape[0]
+    assert f.shape == (n, n, n)
+    total = lib().orc_surface(n, _dp(f.reshape(-1)), float(iso), float(dx), ct.cast(None, _D), 0)
+    out = np.zeros(max(total, 1) * 9)
+    lib().orc_surface(n, _dp(f.reshape(-1)), float(iso), float(dx), _dp(out), total)
+    return out[:total * 9].reshape(total, 3, 3)

@@ -54,6 +54,14 @@ MUTATIONS = {
                                                        "s += 2.0 * taub[3 * a + c] * Fp[3 * c + b];"),
     "adjoint lambda uses J": ("lame_bar[1] += trb * (J > 0.0 ? log(J) : log(1e-6));", "lame_bar[1] += trb * J;"),
     "adjoint dpos term dropped in P2G": ("xbp[b] -= wip * am;", "xbp[b] -= 0.0 * am;"),
+    "surface tetrahedra do not tile the cell": ("{{1, 3}, {1, 5}, {2, 3}, {2, 6}, {4, 5}, {4, 6}}",
+                                                "{{1, 3}, {1, 5}, {2, 3}, {2, 6}, {4, 5}, {4, 5}}"),
+    "surface edge point from either end": ("    if (a > b) { const int t = a; a = b; b = t; }\n    int pa[3], pb[3];",
+                                           "    int pa[3], pb[3];"),
+    "surface lone vertex odd permutation": ("{1, 0, 3, 2}, {2, 0, 1, 3}", "{1, 0, 2, 3}, {2, 0, 1, 3}"),
+    "surface quad parity ignored": ("if (inv & 1) { const int x = perm[2];", "if (0) { const int x = perm[2];"),
+    "surface interpolation from the wrong end": ("const double t = (iso - f[a]) / (f[b] - f[a]);",
+                                                 "const double t = (f[b] - iso) / (f[b] - f[a]);"),
     "block key axis order": ("keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));", "keys[q] = (uint32_t)(b[2] + nb * (b[1] + nb * b[0]));"),
 }
 
@@ -71,6 +79,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     env = dict(os.environ, ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_adjoint_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_adjoint_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_surface_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, "planted mistake '%s' passed every pin" % name
