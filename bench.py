@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true", help="skip the 30K slab line")
     ap.add_argument("--no-differentiable", action="store_true", help="skip the differentiable-rollout line")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default fused-kernel configuration")
+    ap.add_argument("--no-surface", action="store_true", help="skip the surface-extraction line")
     ap.add_argument("--kernel-config", type=int, default=None,
                     help="fused-kernel configuration to use instead of autotuning (MPM_KERNEL_*)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -380,6 +381,47 @@ def run_differentiable(args, rank, device, barrier, max_over_ranks, reps=2):
     return res
 
 
+def run_surface(args, rank, device, barrier, max_over_ranks, reps=10):
+    """Surface extraction (the renderer's Marching Cubes step) of the 1M
+    block after one 25-sub-step frame: the triangles of density 1/2 written
+    to device memory, timed with CUDA events (counts, scan, total readback,
+    triangles)."""
+    import ctypes as ct
+    import torch
+    from paper_2402_01181_gb300 import dist as D
+    from paper_2402_01181_gb300 import mpm
+    sc = scenes.block1m(seed=D.replica_seed(rank))
+    sim = mpm.sim_from_scene(sc)
+    tool = sc.tools[0]
+    sim.set_tool(0, tool.pose(24), tool.shape)
+    sim.step(25)
+    n_tri = ct.c_int64()
+    mpm.check(mpm.mpm_extract_surface(sim.h, 0, 0.5, None, 0, ct.byref(n_tri), 0))
+    T = n_tri.value
+    out = torch.empty((max(T, 1), 9), dtype=torch.float32, device=device)
+    stream = torch.cuda.current_stream(device)
+    times = []
+    for r in range(reps + 2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mpm.check(mpm.mpm_extract_surface(sim.h, 0, 0.5, ct.c_void_p(out.data_ptr()), T, ct.byref(n_tri), 1))
+        b.record(stream)
+        torch.cuda.synchronize(device)
+        if r >= 2:
+            times.append(a.elapsed_time(b))
+    sim.close()
+    ms = max_over_ranks(sorted(times)[len(times) // 2])
+    n = sc.n_grid
+    cells = (n - 1) ** 3
+    # algorithmic bytes: the node masses read by both passes (4 B per node
+    # each), the per-cell counts written, scanned and read (about 16 B per
+    # cell), and the triangles written (36 B each)
+    algo = 2 * 4 * n ** 3 + 16 * cells + 36 * T
+    return {"workload": "block1m surface", "n_grid": n, "triangles": T, "ms": ms,
+            "triangles_per_s": T / (ms / 1e3), "algorithmic_bytes": algo,
+            "achieved_gbs": algo / (ms / 1e3) / 1e9, "note": "median of %d; includes one 4-byte readback" % reps}
+
+
 def algorithmic_bytes_per_particle_step(n, active_nodes, S):
     """Minimum DRAM traffic of one fused sub-step, per particle: the particle
     state is read and written once (x, id: 16 B; F: 36 B; twice = 104 B); each
@@ -485,6 +527,9 @@ def main():
     differentiable = None
     if not args.no_differentiable:
         differentiable = run_differentiable(args, rank, device, barrier, max_over_ranks)
+    surface = None
+    if not args.no_surface:
+        surface = run_surface(args, rank, device, barrier, max_over_ranks)
 
     if rank != 0:
         ranks.close()
@@ -551,6 +596,7 @@ def main():
         "secondary": second,
         "batched": batched,
         "differentiable": differentiable,
+        "surface": surface,
     }
     print(json.dumps(line))
     ranks.close()

@@ -221,6 +221,24 @@ mpm_status mpm_grid_velocity(mpm_handle *h, float *v, int on_device);
  * Host arrays of n entries.  Synchronises. */
 mpm_status mpm_read_order(mpm_handle *h, uint32_t *ids, uint32_t *keys);
 
+/* ------------------------------------------------------- surface extraction */
+
+/* Iso-surface of environment env's tissue: the renderer's Marching Cubes
+ * step of Sec. III, on the grid the next sub-step starts from.  The field
+ * is the node density m_i / (rho dx^3) (about 1 inside the body, 0 outside);
+ * the surface is density = iso, facing away from density >= iso.  Each grid
+ * cell is split into six tetrahedra around its diagonal from its lowest to
+ * its highest corner, each contributing 0, 1 or 2 triangles; the surface is
+ * closed wherever it stays inside the grid.  Vertices are linear
+ * interpolations on tetrahedron edges.  tri: up to max_tri triangles of 9
+ * floats (three vertices x, y, z in metres), in cell order (i fastest, then
+ * j, then k) and a fixed order inside a cell; *n_tri receives the total
+ * (which may exceed max_tri: call again with a larger array).  on_device !=
+ * 0: tri is a device pointer; otherwise a host array (the handle keeps a
+ * device staging buffer).  Synchronises. */
+mpm_status mpm_extract_surface(mpm_handle *h, int32_t env, float iso, float *tri, int64_t max_tri,
+                               int64_t *n_tri, int on_device);
+
 /* ------------------------------------------------------------ kernel tuning */
 
 /* Configurations of the fused sub-step kernel: CTA size x passes of particles

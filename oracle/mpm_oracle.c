@@ -1019,14 +1019,14 @@ static int64_t tet_triangles(const int *cell, const int *t, const double *f, dou
 
 /* field: n^3 node values, [i][j][k] with k fastest; node (i, j, k) sits at
  * (i, j, k) dx.  Writes up to max_tri triangles (9 doubles each: three
- * vertices) in cell order (i, j, k) with k fastest, tetrahedra in the order
- * of orc_tet_paths; returns the total number of triangles. */
+ * vertices) in cell order with i fastest, then j, then k, tetrahedra in the
+ * order of orc_tet_paths; returns the total number of triangles. */
 int64_t orc_surface(int32_t n, const double *field, double iso, double dx, double *out, int64_t max_tri)
 {
     int64_t cnt = 0;
-    for (int i = 0; i + 1 < n; ++i)
+    for (int k = 0; k + 1 < n; ++k)
         for (int j = 0; j + 1 < n; ++j)
-            for (int k = 0; k + 1 < n; ++k) {
+            for (int i = 0; i + 1 < n; ++i) {
                 const int cell[3] = {i, j, k};
                 double f[8];
                 for (int c = 0; c < 8; ++c) {

@@ -482,7 +482,8 @@ def rollout_loss_and_gradients(prm: OracleParams, st0: State, tools, pose_init, 
 
 def surface(field, iso, dx):
     """Triangles (T, 3, 3) of the iso-surface field >= iso of an n^3 node
-    field ([i, j, k], node (i, j, k) at (i, j, k) dx), in cell order."""
+    field ([i, j, k], node (i, j, k) at (i, j, k) dx), in cell order (i
+    fastest, then j, then k)."""
     f = np.ascontiguousarray(field, dtype=np.float64)
     n = f.shape[0]
     assert f.shape == (n, n, n)

@@ -134,6 +134,10 @@ struct mpm_handle {
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     bool use_graphs = true;
     Tape tape;
+    // surface extraction scratch
+    uint32_t *surf_counts = nullptr, *surf_sums = nullptr;
+    float *surf_tri = nullptr;
+    size_t surf_tri_cap = 0;
 };
 
 namespace {
@@ -1231,6 +1235,58 @@ mpm_status mpm_autotune(mpm_handle *h, int32_t n_substeps, float *times_ms, int3
     if (st != MPM_OK) return st;
     if (st2 != MPM_OK) return st2;
     if (best) *best = pick;
+    return MPM_OK;
+}
+
+}  // extern "C"
+
+// ===================================================== surface extraction
+
+extern "C" {
+
+mpm_status mpm_extract_surface(mpm_handle *h, int32_t env, float iso, float *tri, int64_t max_tri, int64_t *n_tri,
+                               int on_device) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (!n_tri) return fail(MPM_ERR_ARG, "NULL n_tri");
+    if (env < 0 || env >= h->n_envs) return fail(MPM_ERR_ARG, "environment %d out of range", env);
+    if (max_tri < 0 || (max_tri > 0 && !tri)) return fail(MPM_ERR_ARG, "need max_tri >= 0 and an output array");
+    if (!std::isfinite(iso)) return fail(MPM_ERR_ARG, "non-finite iso");
+    if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
+    const int n = h->P.n;
+    const size_t cells = (size_t)(n - 1) * (n - 1) * (n - 1);
+    const size_t nblk = (cells + 1 + 1023) / 1024;
+    if (!h->surf_counts) {
+        if ((st = dalloc_t(h, &h->surf_counts, cells + 1)) != MPM_OK) return st;
+        if ((st = dalloc_t(h, &h->surf_sums, nblk + 1)) != MPM_OK) return st;
+    }
+    const float4 *G = current_grid(h);
+    const double dx = 1.0 / n;
+    const float scale = (float)(1.0 / (h->env_rho[env] * dx * dx * dx));   // density / rho
+    launch_surface_count_scan(G, n, h->P.nb, h->nbe, (uint32_t)env, scale, iso, h->surf_counts, h->surf_sums,
+                              h->elem_grid, h->stream);
+    CK(cudaGetLastError());
+    uint32_t total = 0;
+    CK(cudaMemcpyAsync(&total, h->surf_counts + cells, sizeof total, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *n_tri = total;
+    const uint64_t nwrite = std::min<uint64_t>(total, (uint64_t)max_tri);
+    if (nwrite == 0) return MPM_OK;
+    float *dst = tri;
+    if (!on_device) {
+        size_t cap = h->surf_tri_cap;
+        if (cap < nwrite) {   // the old buffer stays with the handle until mpm_destroy
+            if ((st = ensure(h, &h->surf_tri, &cap, 9 * (size_t)nwrite)) != MPM_OK) return st;
+            h->surf_tri_cap = nwrite;
+        }
+        dst = h->surf_tri;
+    }
+    launch_surface_emit(G, n, h->P.nb, h->nbe, (uint32_t)env, scale, iso, (float)dx, h->surf_counts, dst, nwrite,
+                        h->elem_grid, h->stream);
+    CK(cudaGetLastError());
+    if (!on_device)
+        CK(cudaMemcpyAsync(tri, dst, sizeof(float) * 9 * nwrite, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
     return MPM_OK;
 }
 

@@ -47,6 +47,16 @@ void launch_adj_grid(const DevParams &P, const float4 *G, const ToolFrame *tools
 void launch_adj_p2g(const DevParams &P, const PState &S, const VCState &V, uint32_t n, const float4 *Gb,
                     const AdjState &A, double *lame_bar, int grid, cudaStream_t st);
 
+// kernels_surface.cu: iso-surface of the grid density m / (rho dx^3) of
+// environment env.  counts: (n-1)^3 + 1 entries, left holding the exclusive
+// prefix of the per-cell triangle counts (last entry: the total); sums:
+// ceil(((n-1)^3 + 1) / 1024) + 1 entries.
+void launch_surface_count_scan(const float4 *G, int n, int nb, uint32_t nbe, uint32_t env, float scale, float iso,
+                               uint32_t *counts, uint32_t *sums, int grid, cudaStream_t st);
+// triangles (9 floats each) in cell order, the first max_tri of them
+void launch_surface_emit(const float4 *G, int n, int nb, uint32_t nbe, uint32_t env, float scale, float iso, float dx,
+                         const uint32_t *offsets, float *tri, uint64_t max_tri, int grid, cudaStream_t st);
+
 // kernels_sort.cu: stable counting sort of particles by grid block at load.
 struct SortScratch {
     uint32_t *keys;     // n

@@ -88,6 +88,8 @@ SIGNATURES = [
                                          ct.POINTER(ct.c_int32)]),
     ("mpm_tape_record", ct.c_int, [ct.c_void_p, ct.c_int32, _DP, ct.c_int32]),
     ("mpm_set_kernel_config", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("mpm_extract_surface", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_float, ct.c_void_p, ct.c_int64,
+                                       ct.POINTER(ct.c_int64), ct.c_int]),
     ("mpm_get_kernel_config", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
                                          ct.POINTER(ct.c_int32)]),
     ("mpm_autotune", ct.c_int, [ct.c_void_p, ct.c_int32, _FP, ct.POINTER(ct.c_int32)]),
@@ -132,6 +134,7 @@ mpm_block_sort_noalloc = lib.mpm_block_sort_noalloc
 mpm_add_sampled_field = lib.mpm_add_sampled_field
 mpm_tape_record = lib.mpm_tape_record
 mpm_set_kernel_config = lib.mpm_set_kernel_config
+mpm_extract_surface = lib.mpm_extract_surface
 mpm_get_kernel_config = lib.mpm_get_kernel_config
 mpm_autotune = lib.mpm_autotune
 mpm_tape_backward = lib.mpm_tape_backward
@@ -293,6 +296,21 @@ class Sim:
         p = np.ascontiguousarray(np.asarray(pose, dtype=np.float64).reshape(6))
         s = self._shape_for(shape, field)
         check(mpm_set_tool_pose(self.h, int(tool_id), p.ctypes.data_as(_DP), s.ctypes.data_as(_FP)))
+
+    def extract_surface(self, iso=0.5, env=0, device=False):
+        """Triangles (T, 3, 3) of the iso-surface of the grid density
+        (mpm_extract_surface): a numpy array, or a CUDA tensor if device."""
+        n_tri = ct.c_int64()
+        check(mpm_extract_surface(self.h, int(env), float(iso), None, 0, ct.byref(n_tri), 0))
+        T = n_tri.value
+        if device:
+            torch = self._torch
+            out = torch.empty((max(T, 1), 3, 3), dtype=torch.float32, device="cuda")
+            check(mpm_extract_surface(self.h, int(env), float(iso), ct.c_void_p(out.data_ptr()), T, ct.byref(n_tri), 1))
+            return out[:T]
+        out = np.zeros((max(T, 1), 3, 3), dtype=np.float32)
+        check(mpm_extract_surface(self.h, int(env), float(iso), out.ctypes.data_as(ct.c_void_p), T, ct.byref(n_tri), 0))
+        return out[:T]
 
     def set_kernel_config(self, config):
         check(mpm_set_kernel_config(self.h, int(config)))
