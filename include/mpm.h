@@ -175,6 +175,20 @@ mpm_status mpm_add_sampled_field(mpm_handle *h, int32_t res, const double origin
  * particles per sub-step (MPM_ERR_CAPACITY otherwise). */
 mpm_status mpm_step(mpm_handle *h, int32_t n_substeps);
 
+/* mpm_read_particles without the wait, for streaming positions out while
+ * the next sub-steps run: the state at this point of the handle's stream is
+ * gathered on that stream into one of two device staging buffers, then
+ * copied to the host arrays on a separate copy stream, overlapping the
+ * sub-steps enqueued after it.  Host arrays (page-locked for the overlap),
+ * any may be NULL.  The arrays of a call may be read once mpm_wait_read
+ * (or a later call that waits) returns; a call waits on the GPU for the copy
+ * two calls earlier before it refills that staging buffer. */
+mpm_status mpm_read_particles_async(mpm_handle *h, float *x, float *v, float *F, float *C);
+
+/* Wait for every copy mpm_read_particles_async started; returns the sticky
+ * device status seen so far. */
+mpm_status mpm_wait_read(mpm_handle *h);
+
 /* Copy the particle state out in load order (n = the loaded count).  Any of
  * x (n x 3), v (n x 3), F (n x 9), C (n x 9) may be NULL to skip it.
  * on_device != 0: device pointers; otherwise host pointers.  Synchronises

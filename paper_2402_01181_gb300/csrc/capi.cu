@@ -134,6 +134,14 @@ struct mpm_handle {
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
     bool use_graphs = true;
     Tape tape;
+    // asynchronous readback: two staging buffers (24 floats per particle), a
+    // copy stream, and per buffer the events "gathered" and "copied"
+    float *rb_stage[2] = {nullptr, nullptr};
+    size_t rb_cap = 0;
+    cudaStream_t rb_stream = nullptr;
+    cudaEvent_t rb_gathered[2] = {nullptr, nullptr}, rb_copied[2] = {nullptr, nullptr};
+    int rb_next = 0;
+    bool rb_used[2] = {false, false};
     // surface extraction scratch
     uint32_t *surf_counts = nullptr, *surf_sums = nullptr;
     float *surf_tri = nullptr;
@@ -168,6 +176,16 @@ mpm_status dalloc_t(mpm_handle *h, T **out, size_t count) {
 
 void release_all(mpm_handle *h) {
     cudaStreamSynchronize(h->stream);
+    if (h->rb_stream) {
+        cudaStreamSynchronize(h->rb_stream);
+        cudaStreamDestroy(h->rb_stream);
+        h->rb_stream = nullptr;
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (h->rb_gathered[b]) cudaEventDestroy(h->rb_gathered[b]);
+        if (h->rb_copied[b]) cudaEventDestroy(h->rb_copied[b]);
+        h->rb_gathered[b] = h->rb_copied[b] = nullptr;
+    }
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.second);
     h->graphs.clear();
     for (auto &a : h->allocs) {
@@ -1288,6 +1306,58 @@ mpm_status mpm_extract_surface(mpm_handle *h, int32_t env, float iso, float *tri
         CK(cudaMemcpyAsync(tri, dst, sizeof(float) * 9 * nwrite, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     return MPM_OK;
+}
+
+}  // extern "C"
+
+// ================================================== asynchronous readback
+
+extern "C" {
+
+mpm_status mpm_read_particles_async(mpm_handle *h, float *x, float *v, float *F, float *C) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
+    const size_t N = (size_t)h->n;
+    if (N == 0) return MPM_OK;
+    if (!h->rb_stream) {
+        CK(cudaStreamCreateWithFlags(&h->rb_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            CK(cudaEventCreateWithFlags(&h->rb_gathered[b], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->rb_copied[b], cudaEventDisableTiming));
+        }
+    }
+    if (h->rb_cap < 24 * N) {   // a smaller earlier pair stays with the handle until mpm_destroy
+        CK(cudaStreamSynchronize(h->rb_stream));
+        for (int b = 0; b < 2; ++b)
+            if ((st = dalloc_t(h, &h->rb_stage[b], 24 * N)) != MPM_OK) return st;
+        h->rb_cap = 24 * N;
+        h->rb_used[0] = h->rb_used[1] = false;
+    }
+    const int b = h->rb_next;
+    h->rb_next ^= 1;
+    // the copy two reads ago out of this staging buffer must be done before it is refilled
+    if (h->rb_used[b]) CK(cudaStreamWaitEvent(h->stream, h->rb_copied[b], 0));
+    float *sx = h->rb_stage[b], *sv = sx + 3 * N, *sF = sv + 3 * N, *sC = sF + 9 * N;
+    launch_read_out(cur_state(h), h->fb.vc, (uint32_t)N, x ? sx : nullptr, v ? sv : nullptr, F ? sF : nullptr,
+                    C ? sC : nullptr, h->elem_grid, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(h->rb_gathered[b], h->stream));
+    CK(cudaStreamWaitEvent(h->rb_stream, h->rb_gathered[b], 0));
+    if (x) CK(cudaMemcpyAsync(x, sx, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->rb_stream));
+    if (v) CK(cudaMemcpyAsync(v, sv, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->rb_stream));
+    if (F) CK(cudaMemcpyAsync(F, sF, sizeof(float) * 9 * N, cudaMemcpyDeviceToHost, h->rb_stream));
+    if (C) CK(cudaMemcpyAsync(C, sC, sizeof(float) * 9 * N, cudaMemcpyDeviceToHost, h->rb_stream));
+    CK(cudaEventRecord(h->rb_copied[b], h->rb_stream));
+    h->rb_used[b] = true;
+    return MPM_OK;
+}
+
+mpm_status mpm_wait_read(mpm_handle *h) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    if (h->rb_stream) CK(cudaStreamSynchronize(h->rb_stream));
+    return poll_error(h, false);
 }
 
 }  // extern "C"

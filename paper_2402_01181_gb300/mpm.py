@@ -88,6 +88,8 @@ SIGNATURES = [
                                          ct.POINTER(ct.c_int32)]),
     ("mpm_tape_record", ct.c_int, [ct.c_void_p, ct.c_int32, _DP, ct.c_int32]),
     ("mpm_set_kernel_config", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("mpm_read_particles_async", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    ("mpm_wait_read", ct.c_int, [ct.c_void_p]),
     ("mpm_extract_surface", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_float, ct.c_void_p, ct.c_int64,
                                        ct.POINTER(ct.c_int64), ct.c_int]),
     ("mpm_get_kernel_config", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
@@ -134,6 +136,8 @@ mpm_block_sort_noalloc = lib.mpm_block_sort_noalloc
 mpm_add_sampled_field = lib.mpm_add_sampled_field
 mpm_tape_record = lib.mpm_tape_record
 mpm_set_kernel_config = lib.mpm_set_kernel_config
+mpm_read_particles_async = lib.mpm_read_particles_async
+mpm_wait_read = lib.mpm_wait_read
 mpm_extract_surface = lib.mpm_extract_surface
 mpm_get_kernel_config = lib.mpm_get_kernel_config
 mpm_autotune = lib.mpm_autotune
