@@ -228,7 +228,7 @@ def run_gpu_workload(name, args, rank, device, barrier, max_over_ranks, with_e2e
 
 
 def run_batched(args, rank, device, barrier, max_over_ranks, steps=6, loop_steps=2):
-    """Batched environments (SURVEY config 4): n_envs independent slab scenes
+    """Batched environments: n_envs independent slab scenes
     of 5K-40K particles on their own 64^3 grids, stepped by one handle (one
     fused launch per sub-step over all environments), against the per-env
     loop of n_envs single-environment handles on the same GPU.  Metric:
@@ -323,7 +323,7 @@ def run_batched(args, rank, device, barrier, max_over_ranks, steps=6, loop_steps
 
 
 def run_differentiable(args, rank, device, barrier, max_over_ranks, reps=2):
-    """The differentiable rollout (SURVEY config 5): the 30K slab over 500
+    """The differentiable rollout: the 30K slab over 500
     sub-steps with checkpoints every 50, loss = mean |x(T) - target|^2 with
     a target rolled out on the GPU with E = 1.2e4, nu = 0.33 and shifted
     poses.  Times the recorded forward pass (mpm_tape_record) and the reverse
