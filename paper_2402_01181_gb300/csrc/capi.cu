@@ -142,6 +142,9 @@ struct mpm_handle {
     cudaEvent_t rb_gathered[2] = {nullptr, nullptr}, rb_copied[2] = {nullptr, nullptr};
     int rb_next = 0;
     bool rb_used[2] = {false, false};
+    // autotuner snapshot (24 floats per particle), reused by later calls
+    float *tune_snap = nullptr;
+    size_t tune_cap = 0;
     // surface extraction scratch
     uint32_t *surf_counts = nullptr, *surf_sums = nullptr;
     float *surf_tri = nullptr;
@@ -1207,8 +1210,8 @@ mpm_status mpm_autotune(mpm_handle *h, int32_t n_substeps, float *times_ms, int3
     }
     // snapshot of the state, the tools and the counters; every trial starts from it
     const size_t n = (size_t)h->n;
-    float *snap = nullptr;
-    if ((st = dalloc_t(h, &snap, 24 * n)) != MPM_OK) return st;   // kept by the handle until destroy
+    if ((st = ensure(h, &h->tune_snap, &h->tune_cap, 24 * n)) != MPM_OK) return st;
+    float *snap = h->tune_snap;
     float *sx = snap, *sv = snap + 3 * n, *sF = snap + 6 * n, *sC = snap + 15 * n;
     if ((st = mpm_read_particles(h, sx, sv, sF, sC, 1)) != MPM_OK) return st;
     const std::vector<HostTool> tools0 = h->tools;
