@@ -465,13 +465,8 @@ def time_oracle(name, budget_s, rank_seed=0, max_steps=50):
 def reference_main(args):
     from paper_2402_01181_gb300 import dist as D
     world, rank, local = D.env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
-        if rank != 0:
-            dist.barrier()
-            dist.destroy_process_group()
-            return
+    if rank != 0:          # under torchrun only rank 0 times the oracle; the others exit at once
+        return
     budget = 8.0
     vals = []
     for _ in range(args.warmup):
@@ -491,10 +486,6 @@ def reference_main(args):
                              "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.destroy_process_group()
 
 
 # ------------------------------------------------------------------ main
