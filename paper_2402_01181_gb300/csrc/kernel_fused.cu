@@ -206,10 +206,6 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
     const uint32_t nbe = P.nbe;
     uint32_t err = 0;
 
-    // 0. clear the grid blocks G_{k-1} touched, so that sub-step k+1 can scatter into it
-    for (uint32_t q = blockIdx.x * T + tid; q < nclr * 64u; q += gridDim.x * T)
-        Gclr[clr[q >> 6] * 64u + (q & 63u)] = make_float4(0.f, 0.f, 0.f, 0.f);
-
     // prologue: work item blockIdx.x first (the shared counter hands out items
     // gridDim.x, gridDim.x + 1, ... afterwards) and its inputs
     if (tid == T - 1) {
@@ -219,6 +215,10 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
     }
     __syncthreads();
     if (s.items[0] < nact) prefetch_block<T>(s, 0, s.bids[0], inbox_in, Gcur, P, tools, tid);
+    // 0. while the first block's inputs land: clear the grid blocks G_{k-1} touched,
+    //    so that sub-step k+1 can scatter into it (a different buffer from G_k)
+    for (uint32_t q = blockIdx.x * T + tid; q < nclr * 64u; q += gridDim.x * T)
+        Gclr[clr[q >> 6] * 64u + (q & 63u)] = make_float4(0.f, 0.f, 0.f, 0.f);
     cp_async_wait_all();
     __syncthreads();
 
