@@ -63,5 +63,11 @@ def test_argument_validation_without_gpu(lib):
     assert lib.mpm_set_kernel_config(None, 0) == lib.MPM_ERR_ARG
     assert lib.mpm_autotune(None, 1, None, None) == lib.MPM_ERR_ARG
     assert lib.mpm_tape_record(None, 1, None, 1) == lib.MPM_ERR_ARG
+    assert lib.mpm_tape_backward(None, None, None, None, None, 0, None, None, None, None, None, None) == lib.MPM_ERR_ARG
+    n_tri = ct.c_int64()
+    assert lib.mpm_extract_surface(None, 0, 0.5, None, 0, ct.byref(n_tri), 0) == lib.MPM_ERR_ARG
+    assert lib.mpm_read_particles_async(None, None, None, None, None) == lib.MPM_ERR_ARG
+    assert lib.mpm_wait_read(None) == lib.MPM_ERR_ARG
+    assert lib.mpm_get_kernel_config(None, None, None, None) == lib.MPM_ERR_ARG
     assert lib.mpm_destroy(None) == lib.MPM_ERR_ARG
     assert lib.mpm_read_particles(None, None, None, None, None, 0) == lib.MPM_ERR_ARG
