@@ -381,31 +381,55 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
                 bspline_weights(fx, wx);
                 bspline_weights(fy, wy);
                 bspline_weights(fz, wz);
-                float B9[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                // With the stencil offset o = (ii, jj, kk) - f (cell units), the
+                // affine sum of Eq. 9 is sum w v o^T = sum w v (ii, jj, kk)^T - v f^T:
+                // the moments about the stencil base need no per-node offset and
+                // vanish on the ii = 0 (jj = 0, kk = 0) layers.  The x and y
+                // components run on the packed f32x2 pipe.
+                const float2 w0 = make_float2(wx[0], wx[0]), w1 = make_float2(wx[1], wx[1]);
+                const float2 w2 = make_float2(wx[2], wx[2]), w2d = make_float2(2.f * wx[2], 2.f * wx[2]);
+                float2 vxy = make_float2(0.f, 0.f), mxy = vxy, myy = vxy, mzy = vxy;   // v, and moments along x, y, z
+                float vzz = 0.f, mxz = 0.f, myz = 0.f, mzz = 0.f;
 #pragma unroll
                 for (int kk = 0; kk < 3; ++kk) {
 #pragma unroll
                     for (int jj = 0; jj < 3; ++jj) {
                         const float wjk = wy[jj] * wz[kk];
+                        const float2 wjk2 = make_float2(wjk, wjk);
                         const float4 *row = &gv[lx + 6 * (ly + jj) + 36 * (lz + kk)];
-                        float ax = 0.f, ay = 0.f, az = 0.f, bxx = 0.f, bxy = 0.f, bxz = 0.f;
-#pragma unroll
-                        for (int ii = 0; ii < 3; ++ii) {
-                            const float4 g = row[ii];
-                            const float wi = wx[ii], wo = wx[ii] * (ii - fx);
-                            ax += wi * g.x; ay += wi * g.y; az += wi * g.z;
-                            bxx += wo * g.x; bxy += wo * g.y; bxz += wo * g.z;
+                        const float4 g0 = row[0], g1 = row[1], g2 = row[2];
+                        // a = sum_ii wx g, b = sum_ii ii wx g along the row
+                        float2 axy = __fmul2_rn(w0, make_float2(g0.x, g0.y));
+                        axy = __ffma2_rn(w1, make_float2(g1.x, g1.y), axy);
+                        axy = __ffma2_rn(w2, make_float2(g2.x, g2.y), axy);
+                        const float az = fmaf(wx[2], g2.z, fmaf(wx[1], g1.z, wx[0] * g0.z));
+                        const float2 bxy = __ffma2_rn(w2d, make_float2(g2.x, g2.y), __fmul2_rn(w1, make_float2(g1.x, g1.y)));
+                        const float bz = fmaf(w2d.x, g2.z, wx[1] * g1.z);
+                        vxy = __ffma2_rn(wjk2, axy, vxy);
+                        vzz = fmaf(wjk, az, vzz);
+                        mxy = __ffma2_rn(wjk2, bxy, mxy);
+                        mxz = fmaf(wjk, bz, mxz);
+                        if (jj > 0) {
+                            const float2 s2 = jj == 1 ? wjk2 : __fadd2_rn(wjk2, wjk2);
+                            myy = __ffma2_rn(s2, axy, myy);
+                            myz = fmaf(s2.x, az, myz);
                         }
-                        const float dy = wjk * (jj - fy), dz = wjk * (kk - fz);
-                        vx += wjk * ax; vy += wjk * ay; vz += wjk * az;
-                        B9[0] += wjk * bxx; B9[3] += wjk * bxy; B9[6] += wjk * bxz;
-                        B9[1] += dy * ax; B9[4] += dy * ay; B9[7] += dy * az;
-                        B9[2] += dz * ax; B9[5] += dz * ay; B9[8] += dz * az;
+                        if (kk > 0) {
+                            const float2 s2 = kk == 1 ? wjk2 : __fadd2_rn(wjk2, wjk2);
+                            mzy = __ffma2_rn(s2, axy, mzy);
+                            mzz = fmaf(s2.x, az, mzz);
+                        }
                     }
                 }
+                vx = vxy.x; vy = vxy.y; vz = vzz;
+                // C = (4 / dx^2) sum w v (x_i - x_p)^T = (4 / dx) (moments - v f^T)   (Eq. 9)
                 const float cs = 4.0f * P.inv_dx;
-#pragma unroll
-                for (int q = 0; q < 9; ++q) Cm[q] = cs * B9[q];
+                const float2 cxy = __ffma2_rn(make_float2(-fx, -fx), vxy, mxy);
+                const float2 cyy = __ffma2_rn(make_float2(-fy, -fy), vxy, myy);
+                const float2 czy = __ffma2_rn(make_float2(-fz, -fz), vxy, mzy);
+                Cm[0] = cs * cxy.x; Cm[1] = cs * cyy.x; Cm[2] = cs * czy.x;
+                Cm[3] = cs * cxy.y; Cm[4] = cs * cyy.y; Cm[5] = cs * czy.y;
+                Cm[6] = cs * fmaf(-fx, vzz, mxz); Cm[7] = cs * fmaf(-fy, vzz, myz); Cm[8] = cs * fmaf(-fz, vzz, mzz);
                 // --- Eq. 4 and Eq. 10
 #pragma unroll
                 for (int r = 0; r < 3; ++r)
@@ -581,27 +605,44 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
                     bspline_weights(s.st_f[0][q], wx);
                     bspline_weights(s.st_f[1][q], wy);
                     bspline_weights(s.st_f[2][q], wz);
-                    // momentum inputs in fixed-point units
-                    float A[9];
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) A[c] = s.st_a[c][q] * sv;
-                    const float qx = s.st_q[0][q] * sv, qy = s.st_q[1][q] * sv, qz = s.st_q[2][q] * sv;
+                    // momentum inputs in fixed-point units, as (x, y) and (z, mass)
+                    // pairs for the packed f32x2 pipe: the value at stencil offset
+                    // (ii, jj, kk) is q + A' (ii, jj, kk), the mass term the constant
+                    // kFix (m_p 2^22 in mass units)
+                    const float2 sv2 = make_float2(sv, sv), two = make_float2(2.f, 2.f);
+                    const float2 qxy = __fmul2_rn(make_float2(s.st_q[0][q], s.st_q[1][q]), sv2);
+                    const float2 qzm = make_float2(s.st_q[2][q] * sv, kFix);
+                    const float2 aixy = __fmul2_rn(make_float2(s.st_a[0][q], s.st_a[3][q]), sv2);
+                    const float2 ajxy = __fmul2_rn(make_float2(s.st_a[1][q], s.st_a[4][q]), sv2);
+                    const float2 akxy = __fmul2_rn(make_float2(s.st_a[2][q], s.st_a[5][q]), sv2);
+                    const float2 aizm = make_float2(s.st_a[6][q] * sv, 0.f);
+                    const float2 ajzm = make_float2(s.st_a[7][q] * sv, 0.f);
+                    const float2 akzm = make_float2(s.st_a[8][q] * sv, 0.f);
+                    const float2 mm = make_float2(kMagic, kMagic);
+                    const float2 wxx[3] = {make_float2(wx[0], wx[0]), make_float2(wx[1], wx[1]), make_float2(wx[2], wx[2])};
 #pragma unroll
                     for (int kk = 0; kk < 3; ++kk) {
 #pragma unroll
                         for (int jj = 0; jj < 3; ++jj) {
                             const float wjk = wy[jj] * wz[kk];
-                            const float rx = qx + A[1] * jj + A[2] * kk;
-                            const float ry = qy + A[4] * jj + A[5] * kk;
-                            const float rz = qz + A[7] * jj + A[8] * kk;
+                            const float2 wjk2 = make_float2(wjk, wjk);
+                            float2 rxy = qxy, rzm = qzm;
+                            if (jj == 1) { rxy = __fadd2_rn(rxy, ajxy); rzm = __fadd2_rn(rzm, ajzm); }
+                            if (jj == 2) { rxy = __ffma2_rn(two, ajxy, rxy); rzm = __ffma2_rn(two, ajzm, rzm); }
+                            if (kk == 1) { rxy = __fadd2_rn(rxy, akxy); rzm = __fadd2_rn(rzm, akzm); }
+                            if (kk == 2) { rxy = __ffma2_rn(two, akxy, rxy); rzm = __ffma2_rn(two, akzm, rzm); }
 #pragma unroll
                             for (int ii = 0; ii < 3; ++ii) {
-                                const float w = wx[ii] * wjk;
+                                float2 vxy = rxy, vzm = rzm;
+                                if (ii == 1) { vxy = __fadd2_rn(vxy, aixy); vzm = __fadd2_rn(vzm, aizm); }
+                                if (ii == 2) { vxy = __ffma2_rn(two, aixy, vxy); vzm = __ffma2_rn(two, aizm, vzm); }
+                                const float2 w2 = __fmul2_rn(wxx[ii], wjk2);
+                                const float2 bxy = __ffma2_rn(w2, vxy, mm), bzm = __ffma2_rn(w2, vzm, mm);
                                 const int a = base + ii + kAy * jj + kAz * kk;
-                                atomicAdd(&s.acc[0][a], fix_round(fmaf(w, kFix, kMagic)));
-                                atomicAdd(&s.acc[1][a], fix_round(fmaf(w, rx + A[0] * ii, kMagic)));
-                                atomicAdd(&s.acc[2][a], fix_round(fmaf(w, ry + A[3] * ii, kMagic)));
-                                atomicAdd(&s.acc[3][a], fix_round(fmaf(w, rz + A[6] * ii, kMagic)));
+                                atomicAdd(&s.acc[0][a], fix_round(bzm.y));
+                                atomicAdd(&s.acc[1][a], fix_round(bxy.x));
+                                atomicAdd(&s.acc[2][a], fix_round(bxy.y));
+                                atomicAdd(&s.acc[3][a], fix_round(bzm.x));
                             }
                         }
                     }
