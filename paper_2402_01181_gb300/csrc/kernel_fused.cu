@@ -231,12 +231,11 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
         const int bx = bl % nb, by = (bl / nb) % nb, bz = bl / (nb * nb);
         const EnvParams &ep = s.ep[cb];
         const float m = ep.mass;
-        // the next work item, fetched while this block is set up
-        if (tid == T - 1) {
-            const uint32_t it = gridDim.x + atomicAdd(&ctrl->work, 1u);
-            s.items[cb ^ 1] = it;
-            s.bids[cb ^ 1] = it < nact ? act[it] : 0u;
-        }
+        // the next work item: the atomic is issued here and its result is
+        // consumed after this thread's share of the grid operation
+        uint32_t next_item = 0;
+        if (tid == T - 1) next_item = gridDim.x + atomicAdd(&ctrl->work, 1u);
+        uint32_t alloc_ob = 0, alloc_cf = 0;     // thread 0: the block's output range and chunks
         float4 *gv = s.graw[cb];
 
         // 1. grid operation of the 6^3 G2P region, in place (warps 1 ..)
@@ -250,6 +249,10 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
         for (int q = tid; q < 4 * kArena; q += T) (&s.acc[0][0])[q] = 0;
         if (tid < 32) s.ccount[tid] = 0u;
         for (int q = tid; q < 2 * NW * 28; q += T) (&s.wcnt[0][0][0])[q] = 0u;
+        if (tid == T - 1) {
+            s.items[cb ^ 1] = next_item;
+            s.bids[cb ^ 1] = next_item < nact ? act[next_item] : 0u;
+        }
         // 2. warp 0: the runs heading to b, in ascending source-block order
         //    (direction d = 26 .. 0, source pass 0 .. 3), with their exclusive
         //    prefix = logical index of each run's first particle
@@ -319,31 +322,36 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
             if (lane == 0) {
                 s.ncand = nc;
                 s.cand_pre[nc] = carry;
-                const uint32_t total = carry;
-                s.total = total;
-                const uint32_t npass = (total + T - 1) / T;
-                const uint32_t ob = atomicAdd(&ctrl->part_alloc, total);
-                const uint32_t cf = atomicAdd(&ctrl->chunk_alloc, npass);
-                BlockTab t;
-                t.pad = 0;
-                if (ob + total > nparticles || cf + npass > nchunk_cap) {
-                    err |= kErrCapacity;
-                    s.npass = 0;
-                    t.stamp = 0; t.first = 0; t.npass = 0;
-                } else {
-                    s.npass = npass;
-                    t.stamp = step + 1; t.first = cf; t.npass = npass;
-                }
-                tout[b] = t;
-                s.out_base = ob;
-                s.chunk_first = cf;
+                s.total = carry;
+                s.npass = (carry + T - 1) / T;
+                // issued here, consumed after the barrier below
+                alloc_ob = atomicAdd(&ctrl->part_alloc, carry);
+                alloc_cf = atomicAdd(&ctrl->chunk_alloc, (carry + T - 1) / T);
                 s.mask = 0;
                 s.bmax = 0;
             }
         }
         __syncthreads();
         const uint32_t ncand = s.ncand;
-        const uint32_t total = s.total, npass = s.npass, out_base = s.out_base, chunk_first = s.chunk_first;
+        const uint32_t total = s.total, npass = s.npass;
+        // thread 0: the block's table for the next sub-step and its output range,
+        // read by every thread after the first pass's barrier; if the allocation
+        // overflowed, the range starts past the end of the particle and chunk
+        // arrays and nothing is written
+        if (tid == 0) {
+            BlockTab t;
+            t.pad = 0;
+            const bool fit = alloc_ob + total <= nparticles && alloc_cf + npass <= nchunk_cap;
+            if (fit) {
+                t.stamp = step + 1; t.first = alloc_cf; t.npass = npass;
+            } else {
+                err |= kErrCapacity;
+                t.stamp = 0; t.first = 0; t.npass = 0;
+            }
+            tout[b] = t;
+            s.out_base = fit ? alloc_ob : nparticles;
+            s.chunk_first = fit ? alloc_cf : nchunk_cap;
+        }
         // this thread's particle of the first pass, then the next block's inputs;
         // both land while this block computes
         if (npass > 0 && (uint32_t)tid < total) prefetch_particle(s, in, ncand, (uint32_t)tid, tid);
@@ -522,6 +530,7 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
             uint32_t(*wc)[28] = s.wcnt[pass & 1];
             if (valid && rank == 0) wc[warp][d] = __popc(peers);
             __syncthreads();
+            const uint32_t out_base = s.out_base, chunk_first = s.chunk_first;
             uint32_t run = 0, before = 0;                 // lane l: pass total and earlier warps' count of direction l
             if (lane < 27) {
 #pragma unroll
@@ -541,7 +550,7 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
             // this warp's row of the other parity is next written by this warp, in the
             // next pass; every warp's reads of it ended before the barrier above
             if (lane < 28) s.wcnt[(pass + 1) & 1][warp][lane] = 0u;
-            if (warp == 0) {
+            if (warp == 0 && chunk_first + pass < nchunk_cap) {
                 const uint32_t pbase = out_base + pass * T;
                 if (lane < 27) {
                     cout[chunk_first + pass].run[lane] = make_uint2(pbase + incl - run, run);
@@ -557,8 +566,8 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
                 const unsigned nz = __ballot_sync(0xffffffffu, lane < 27 && run > 0);
                 if (lane == 0) s.mask |= nz;
             }
-            if (valid) {
-                const uint32_t pos = out_base + pass * T + my_off + rank;
+            const uint32_t pos = out_base + pass * T + my_off + rank;
+            if (valid && pos < nparticles) {
                 out.xi[pos] = make_float4(nxp, nyp, nzp, idf);
                 out.f0[pos] = make_float4(Fn[0], Fn[1], Fn[2], Fn[3]);
                 out.f1[pos] = make_float4(Fn[4], Fn[5], Fn[6], Fn[7]);
