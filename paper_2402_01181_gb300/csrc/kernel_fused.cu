@@ -80,7 +80,7 @@ struct FusedSmem {
     uint32_t cand_pre[CMAX + 1];   // exclusive prefix of run lengths
     uint32_t lane_first[27], lane_off[27];
     uint32_t wcnt[2][NW][28];      // per pass parity: per-warp direction counts
-    uint32_t ncand, total, out_base, chunk_first, npass, mask, bmax;
+    uint32_t ncand, total, out_base, chunk_first, npass, mask, bmax, wide;
 };
 
 // resident CTAs per SM for which a configuration is compiled: 228 KB of shared
@@ -215,6 +215,8 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
     }
     __syncthreads();
     if (s.items[0] < nact) prefetch_block<T>(s, 0, s.bids[0], inbox_in, Gcur, P, tools, tid);
+    // the P2G arena starts at zero; every flush returns the nodes it read to zero
+    for (int q = tid; q < 4 * kArena; q += T) (&s.acc[0][0])[q] = 0;
     // 0. while the first block's inputs land: clear the grid blocks G_{k-1} touched,
     //    so that sub-step k+1 can scatter into it (a different buffer from G_k)
     for (uint32_t q = blockIdx.x * T + tid; q < nclr * 64u; q += gridDim.x * T)
@@ -246,7 +248,6 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
             if (i < n && j < n && k < n) v = grid_node_update(g.x, g.y, g.z, g.w, i, j, k, P, s.tools[cb], ep.ntools);
             gv[q] = make_float4(v.x, v.y, v.z, 0.f);
         }
-        for (int q = tid; q < 4 * kArena; q += T) (&s.acc[0][0])[q] = 0;
         if (tid < 32) s.ccount[tid] = 0u;
         for (int q = tid; q < 2 * NW * 28; q += T) (&s.wcnt[0][0][0])[q] = 0u;
         if (tid == T - 1) {
@@ -329,6 +330,7 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
                 alloc_cf = atomicAdd(&ctrl->chunk_alloc, (carry + T - 1) / T);
                 s.mask = 0;
                 s.bmax = 0;
+                s.wide = 0;
             }
         }
         __syncthreads();
@@ -473,6 +475,9 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
                 const int ax0 = hx - ox, ay0 = hy - oy, az0 = hz - oz;
                 const bool in_arena = ax0 >= 0 && ax0 <= 5 && ay0 >= 0 && ay0 <= 5 && az0 >= 0 && az0 <= 5;
                 if (in_arena) {
+                    // a base cell outside b (the particle moved into a neighbour
+                    // block) widens the group's stencils beyond the 6^3 nodes of b
+                    if (ax0 == 0 || ax0 == 5 || ay0 == 0 || ay0 == 5 || az0 == 0 || az0 == 5) s.wide = 1u;
                     const int abase = ax0 + kAy * ay0 + kAz * az0;
                     s.st_base[slot] = abase;
                     const uint32_t cls = (uint32_t)abase & 31u;
@@ -581,6 +586,7 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
             if (pass % GP == GP - 1 || pass + 1 == npass) {
                 const int nstaged = (int)min((uint32_t)GROUP, total - (pass - pass % GP) * T);
                 const float bmax = __uint_as_float(s.bmax);
+                const bool wide = s.wide != 0u;
                 const float sv = bmax > 0.f ? kFix / bmax : 1.0f;   // momentum fixed-point scale
                 // order the group's arena particles by bank bucket (a counting sort over
                 // 32 buckets): lane l of a warp then takes sorted position l * rows + j,
@@ -657,10 +663,17 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
                     }
                 }
                 __syncthreads();
-                // arena -> G_{k+1}, then reset it for the next group
+                // arena -> G_{k+1}, then reset it for the next group: all 8^3 nodes,
+                // or only the 6^3 around b when every base cell lies in b
                 const float um = m / kFix, up = 1.0f / sv;
-                for (int q = tid; q < 512; q += T) {
-                    const int lx8 = q & 7, ly8 = (q >> 3) & 7, lz8 = q >> 6;
+                const int nflush = wide ? 512 : 216;
+                for (int q = tid; q < nflush; q += T) {
+                    int lx8, ly8, lz8;
+                    if (wide) {
+                        lx8 = q & 7; ly8 = (q >> 3) & 7; lz8 = q >> 6;
+                    } else {
+                        lx8 = 1 + q % 6; ly8 = 1 + (q / 6) % 6; lz8 = 1 + q / 36;
+                    }
                     const int a = lx8 + kAy * ly8 + kAz * lz8;
                     const int am = s.acc[0][a], px = s.acc[1][a], py = s.acc[2][a], pz = s.acc[3][a];
                     if (am != 0 || px != 0 || py != 0 || pz != 0) {
@@ -671,9 +684,9 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
                         s.acc[0][a] = 0; s.acc[1][a] = 0; s.acc[2][a] = 0; s.acc[3][a] = 0;
                     }
                 }
-                // every thread read s.bmax and the bucket sizes before the barriers
+                // every thread read s.bmax, s.wide and the bucket sizes before the barriers
                 // above; the next group's atomics come after the barrier below
-                if (tid == 0) s.bmax = 0;
+                if (tid == 0) { s.bmax = 0; s.wide = 0; }
                 if (tid < 32) s.ccount[tid] = 0u;
                 __syncthreads();
             }
