@@ -26,6 +26,7 @@ this method to compare with.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -87,33 +88,102 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+class _Nvml:
+    """Read-only NVML queries (SM clock, its maximum, clock-event reasons)
+    through libnvidia-ml, the library nvidia-smi itself reads."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index):
+        import ctypes as ct
+        self.ct = ct
+        self.lib = ct.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ct.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ct.c_uint(index), ct.byref(self.h)) != 0:
+            raise RuntimeError("no NVML device %d" % index)
+        self.get_reasons = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def _clock(self, fn):
+        v = self.ct.c_uint(0)
+        return float(v.value) if fn(self.h, 1, self.ct.byref(v)) == 0 else None     # 1: the SM clock domain
+
+    def sm_clock(self):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo)
+
+    def sm_max_clock(self):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo)
+
+    def reasons(self):
+        r = self.ct.c_ulonglong(0)
+        if self.get_reasons(self.h, self.ct.byref(r)) != 0:
+            return []
+        return [nm for bit, nm in self.REASONS.items() if r.value & bit]
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """SM clock and clock-event reasons during the timed region.  NVML is
+    polled every 5 ms on a background thread, and nvidia-smi samples every
+    50 ms alongside it; both run from before the warm-up to after the timed
+    region, and summary() keeps the samples taken between mark_start() and
+    mark_end() (NVML's if it loaded, else nvidia-smi's)."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
+    NVML_INTERVAL_S = 0.005
 
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
         self.lines = []
+        self.nvml = None
+        self.nvml_samples = []
+        self.stop = threading.Event()
+        self.t0 = self.t1 = None
+        self.p0 = self.p1 = None
+
+    def mark_start(self):
+        self.t0 = datetime.datetime.now()
+        self.p0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = datetime.datetime.now()
+        self.p1 = time.perf_counter()
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception:
             self.proc = None
+        try:
+            self.nvml = _Nvml(self.dev)
+            self.nvml_max = self.nvml.sm_max_clock()
+            self.tn = threading.Thread(target=self._poll, daemon=True)
+            self.tn.start()
+        except Exception:
+            self.nvml = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def _poll(self):
+        while not self.stop.is_set():
+            self.nvml_samples.append((time.perf_counter(), self.nvml.sm_clock(), self.nvml.reasons()))
+            time.sleep(self.NVML_INTERVAL_S)
+
     def __exit__(self, *a):
+        self.stop.set()
+        if self.nvml is not None:
+            self.tn.join(timeout=2)
         if self.proc:
             self.proc.terminate()
             try:
@@ -121,24 +191,40 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    def _smi_samples(self):
+        out = []
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 7:
+            if len(parts) < 8:
                 continue
+            ts = None
+            for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+                try:
+                    ts = datetime.datetime.strptime(parts[0], fmt)
+                    break
+                except ValueError:
+                    pass
             try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
+                clk, cmax = float(parts[1]), float(parts[2])
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[3:7]):
-                if val.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+            if ts is None or (self.t0 is not None and not (self.t0 <= ts <= (self.t1 or ts))):
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            out.append((clk, cmax, [nm for nm, val in zip(names, parts[4:8]) if val.lower() == "active"]))
+        return out
+
+    def summary(self):
+        smi = self._smi_samples()
+        nv = [(c, self.nvml_max, r) for t, c, r in self.nvml_samples
+              if c is not None and (self.p0 is None or self.p0 <= t <= (self.p1 or t))]
+        src, use = ("nvml", nv) if nv else ("nvidia-smi", smi)
+        if not use:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        reasons = sorted({nm for _, _, r in use for nm in r})
+        return {"sm_mhz": float(np.median([c for c, _, _ in use])), "sm_min_mhz": float(min(c for c, _, _ in use)),
+                "sm_max_mhz": use[-1][1], "reasons": reasons, "samples": len(use), "source": src,
+                "window": "timed region", "nvidia_smi_samples": len(smi)}
 
 
 # ------------------------------------------------------------ GPU workload
@@ -176,19 +262,21 @@ def run_gpu_workload(name, args, rank, device, barrier, max_over_ranks, with_e2e
     active_nodes = int((grid[..., 0] > 0).sum())
     del grid
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
-    for _ in range(args.warmup):
-        frame()
-    sim.synchronize()
-    barrier()
-    torch.cuda.synchronize(device)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with ClockSampler(device) as clk:
+        for _ in range(args.warmup):
+            frame()
+        sim.synchronize()
+        barrier()
+        torch.cuda.synchronize(device)
+        clk.mark_start()
         for i in range(steps):
             flush.zero_()
             ev[i][0].record(stream)
             frame()
             ev[i][1].record(stream)
         torch.cuda.synchronize(device)
+        clk.mark_end()
     barrier()
     st = sim.status()
     if st != mpm.MPM_OK:
@@ -473,8 +561,8 @@ def reference_main(args):
         time_oracle(args.workload, budget / 4, max_steps=1)
     t0 = time.perf_counter()
     sample = ""
-    for _ in range(args.steps):
-        v, sample = time_oracle(args.workload, budget, max_steps=3)
+    for _ in range(args.steps):      # one full-size sub-step per step (about 0.5 s for block1m)
+        v, sample = time_oracle(args.workload, budget, max_steps=1)
         vals.append(v)
     el = time.perf_counter() - t0
     value = float(np.mean(vals))

@@ -277,12 +277,12 @@ mpm_status mpm_set_kernel_config(mpm_handle *h, int32_t config);
 mpm_status mpm_get_kernel_config(mpm_handle *h, int32_t *config, int32_t *threads, int32_t *ctas);
 
 /* Autotuner: time every configuration on the handle's own state (one
- * untimed call of n_substeps sub-steps, then one timed call, each trial
+ * untimed call of n_substeps sub-steps, then three timed calls, each trial
  * starting from the same snapshot of the particles and tools), select the
- * fastest and restore the state as it was (particle order inside the
- * library may change; mpm_read_particles returns the same values).
- * times_ms (MPM_KERNEL_CONFIGS floats, -1 for configurations that do not fit)
- * and best may be NULL.  Needs a loaded fused-pipeline handle
+ * one with the smallest median call time and restore the state as it was
+ * (particle order inside the library may change; mpm_read_particles returns
+ * the same values).  times_ms (MPM_KERNEL_CONFIGS floats: the median call
+ * times, -1 for configurations that do not fit) and best may be NULL.  Needs a loaded fused-pipeline handle
  * (MPM_ERR_STATE).  Synchronises; allocates a snapshot of 24 floats per
  * particle, kept by the handle. */
 mpm_status mpm_autotune(mpm_handle *h, int32_t n_substeps, float *times_ms, int32_t *best);

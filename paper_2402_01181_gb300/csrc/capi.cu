@@ -1195,6 +1195,9 @@ mpm_status mpm_get_kernel_config(mpm_handle *h, int32_t *config, int32_t *thread
     return MPM_OK;
 }
 
+// timed calls per configuration in mpm_autotune (their median is compared)
+constexpr int kTuneReps = 3;
+
 mpm_status mpm_autotune(mpm_handle *h, int32_t n_substeps, float *times_ms, int32_t *best) {
     mpm_status st = check_handle(h);
     if (st != MPM_OK) return st;
@@ -1237,14 +1240,21 @@ mpm_status mpm_autotune(mpm_handle *h, int32_t n_substeps, float *times_ms, int3
         if ((st = apply_kernel_config(h, c)) != MPM_OK) break;
         if ((st = restore()) != MPM_OK) break;
         if ((st = mpm_step(h, n_substeps)) != MPM_OK) break;      // captures the graphs
-        h->tools = tools0;
-        cudaEventRecord(a, h->stream);
-        if ((st = mpm_step(h, n_substeps)) != MPM_OK) break;
-        cudaEventRecord(b, h->stream);
-        if (cudaEventSynchronize(b) != cudaSuccess) { st = fail(MPM_ERR_CUDA, "cudaEventSynchronize failed"); break; }
-        if ((st = poll_error(h, true)) != MPM_OK) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
+        // the median of kTuneReps timed calls
+        float reps[kTuneReps];
+        for (int r = 0; r < kTuneReps && st == MPM_OK; ++r) {
+            h->tools = tools0;
+            cudaEventRecord(a, h->stream);
+            if ((st = mpm_step(h, n_substeps)) != MPM_OK) break;
+            cudaEventRecord(b, h->stream);
+            if (cudaEventSynchronize(b) != cudaSuccess) { st = fail(MPM_ERR_CUDA, "cudaEventSynchronize failed"); break; }
+            if ((st = poll_error(h, true)) != MPM_OK) break;
+            reps[r] = 0.f;
+            cudaEventElapsedTime(&reps[r], a, b);
+        }
+        if (st != MPM_OK) break;
+        std::sort(reps, reps + kTuneReps);
+        const float ms = reps[kTuneReps / 2];
         if (times_ms) times_ms[c] = ms;
         if (ms < best_ms) { best_ms = ms; pick = c; }
     }
