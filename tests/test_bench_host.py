@@ -1,0 +1,56 @@
+"""Host logic of bench.py that needs no GPU: the clock sampler keeps only the
+samples taken inside the timed region (NVML's when present, else
+nvidia-smi's), and the oracle timer of the reference arm and of
+cpu_baseline reports a positive rate on a bounded sample."""
+import datetime
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _smi_line(t, clk, cap="Not Active", hw="Not Active"):
+    return "%s, %d, 2070, 900.0, %s, Not Active, Not Active, %s" % (
+        t.strftime("%Y/%m/%d %H:%M:%S.%f")[:-3], clk, hw, cap)
+
+
+def test_clock_sampler_keeps_the_timed_window_from_nvidia_smi():
+    c = bench.ClockSampler(0)
+    now = datetime.datetime.now()
+    sec = lambda x: now + datetime.timedelta(seconds=x)
+    c.lines = [_smi_line(sec(-1.0), 900), _smi_line(sec(0.1), 2070, cap="Active"), _smi_line(sec(0.2), 2050),
+               _smi_line(sec(0.3), 2060), _smi_line(sec(3.0), 600, hw="Active"), "garbage line"]
+    c.t0, c.t1 = now, sec(1.0)
+    s = c.summary()
+    assert s["source"] == "nvidia-smi" and s["samples"] == 3
+    assert s["sm_mhz"] == 2060.0 and s["sm_min_mhz"] == 2050.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]          # the hw_slowdown sample lies outside the window
+
+
+def test_clock_sampler_prefers_nvml_inside_the_window():
+    c = bench.ClockSampler(0)
+    c.p0, c.p1 = 10.0, 11.0
+    c.nvml_max = 2070.0
+    c.nvml_samples = [(9.0, 500.0, ["hw_slowdown"]), (10.2, 2070.0, []), (10.4, 2070.0, []),
+                      (10.6, 2040.0, ["sw_power_cap"]), (10.8, None, []), (12.0, 700.0, [])]
+    s = c.summary()
+    assert s["source"] == "nvml" and s["samples"] == 3
+    assert s["sm_mhz"] == 2070.0 and s["sm_min_mhz"] == 2040.0 and s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_samples_says_so():
+    c = bench.ClockSampler(0)
+    c.p0, c.p1 = 1.0, 2.0
+    s = c.summary()
+    assert s["samples"] == 0 and s["reasons"] == ["unsampled"]
+
+
+def test_oracle_timer_reports_a_bounded_sample():
+    from oracle import oracle as O
+    O.build()
+    rate, sample = bench.time_oracle("cube8k", 2.0, max_steps=2)
+    assert rate > 0 and "cube8k" in sample and sample.startswith(("1 ", "2 "))
