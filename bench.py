@@ -30,6 +30,7 @@ import datetime
 import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import threading
@@ -71,11 +72,20 @@ def parse():
 
 # --------------------------------------------------------------- helpers
 
+def _code_only(text):
+    """C/CUDA source without comments and blank lines, whitespace runs folded."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(" ".join(ln.split()) for ln in text.splitlines() if ln.strip())
+
+
 def kernel_source_sha():
+    """Hash of the fused kernel's code (comments excluded), which the ncu
+    counters in profiles/traffic.json are tied to."""
     h = hashlib.sha256()
     for f in ("kernel_fused.cu", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_2402_01181_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2402_01181_gb300", "csrc", f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -9,15 +9,15 @@
 //   1. grid operation (Eq. 7, gravity, tool contact Eqs. 11, 15-19, walls) of
 //      the 6^3 nodes that the stencils of b's particles touch, into shared
 //      memory;
-//   2. per particle (256-particle passes): G2P (Eqs. 8-9), F update (Eq. 4),
-//      advection (Eq. 10), Kirchhoff stress of the new F (Eqs. 5-6) and the
-//      affine momentum A = m C - dt V^0 (4/dx^2) tau;
+//   2. per particle (passes of one particle per thread): G2P (Eqs. 8-9), F
+//      update (Eq. 4), advection (Eq. 10), Kirchhoff stress of the new F
+//      (Eqs. 5-6) and the affine momentum A = m C - dt V^0 (4/dx^2) tau;
 //   3. a stable counting sort of the particles by their new block: every pass
 //      writes its particles grouped by the direction (-1..1)^3 to their new
 //      block and records where each group starts; the next sub-step's CTA for
 //      block b' reads the runs heading to b' from its 27 neighbours, in
 //      ascending source-block order;
-//   4. P2G (Eqs. 1-3) of up to 512 new particle states at a time into an
+//   4. P2G (Eqs. 1-3) of up to 2 passes of new particle states at a time into an
 //      8^3-node shared arena around b.  The arena accumulates in 32-bit fixed
 //      point with native shared integer atomics (shared float atomics are
 //      several times slower): mass in units of m_p 2^-22, momentum in units of
@@ -27,7 +27,10 @@
 //      the atomics.  A particle that moved further than one cell scatters
 //      straight into G_{k+1} with float atomics instead.
 //   5. the arena is converted back to floats and added to G_{k+1} with float4
-//      atomics.
+//      atomics (only the 6^3 nodes around b when every base cell lies in b),
+//      and the nodes read are returned to zero.
+//
+// G2P and P2G run their x/y (and z/mass) components on the packed f32x2 pipe.
 //
 // Grid buffers rotate over three slots (read G_k, write G_{k+1}, clear
 // G_{k-1} for reuse), particle buffers and run tables over two; the last CTA
