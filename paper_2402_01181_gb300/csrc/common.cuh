@@ -106,8 +106,10 @@ struct Ctrl {
     uint32_t pad3[31];
     uint32_t chunk_alloc;       // chunk entries handed out in the current launch
     uint32_t pad4[31];
-    uint32_t nactive[2];        // active-block list sizes, by sub-step parity
-    uint32_t pad5[30];
+    // active-block list sizes by sub-step parity: [0] heavy blocks, listed from
+    // the front, [1] light blocks, listed from the back (one 64-bit read)
+    uint32_t nactive[2][2];
+    uint32_t pad5[28];
     uint32_t nclear[3];         // grid clear-list sizes, by sub-step mod 3
     uint32_t pad6[29];
 };

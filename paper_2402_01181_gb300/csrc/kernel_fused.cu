@@ -43,6 +43,7 @@ namespace gbmpm {
 namespace {
 
 constexpr int CMAX = 512;      // run candidates (source chunk x direction) per block
+constexpr uint32_t kHeavy = 256;        // particles above which a block's item is listed first
 constexpr float kFix = 4194304.0f;      // 2^22
 constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23: float -> nearest int for |v| < 2^22
 // arena node (x, y, z) in [0,8)^3 sits at x + kAy y + kAz z: kAz = 68 keeps the
@@ -200,7 +201,14 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
     uint4 *__restrict__ inbox_out = par ? B.inbox[0] : B.inbox[1];
     const uint32_t *__restrict__ act = B.alist[par];
     uint32_t *act_next = B.alist[par ^ 1];
-    const uint32_t nact = *(volatile uint32_t *)&ctrl->nactive[par];
+    // the active blocks: heavy ones listed from the front, light ones from the
+    // back, and handed out heavy first so that the launch ends on short items
+    const unsigned long long nhl = *(volatile unsigned long long *)&ctrl->nactive[par][0];
+    const uint32_t nheavy = (uint32_t)nhl, nact = (uint32_t)nhl + (uint32_t)(nhl >> 32);
+    const uint32_t acap = B.nblocks;
+    auto item_block = [&](uint32_t it) -> uint32_t {
+        return it >= nact ? 0u : (it < nheavy ? act[it] : act[acap - 1u - (it - nheavy)]);
+    };
     const uint32_t nclr = *(volatile uint32_t *)&ctrl->nclear[m3c];
     const uint32_t *__restrict__ clr = B.clist[m3c];
     const uint32_t nparticles = ctrl->n_particles;
@@ -214,7 +222,7 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
     if (tid == T - 1) {
         const uint32_t it = blockIdx.x;
         s.items[0] = it;
-        s.bids[0] = it < nact ? act[it] : 0u;
+        s.bids[0] = item_block(it);
     }
     __syncthreads();
     if (s.items[0] < nact) prefetch_block<T>(s, 0, s.bids[0], inbox_in, Gcur, P, tools, tid);
@@ -255,7 +263,7 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
         for (int q = tid; q < 2 * NW * 28; q += T) (&s.wcnt[0][0][0])[q] = 0u;
         if (tid == T - 1) {
             s.items[cb ^ 1] = next_item;
-            s.bids[cb ^ 1] = next_item < nact ? act[next_item] : 0u;
+            s.bids[cb ^ 1] = item_block(next_item);
         }
         // 2. warp 0: the runs heading to b, in ascending source-block order
         //    (direction d = 26 .. 0, source pass 0 .. 3), with their exclusive
@@ -702,8 +710,15 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
             if (tx >= 0 && ty >= 0 && tz >= 0 && tx < nb && ty < nb && tz < nb) {
                 const uint32_t tb = eb0 + block_id(tx, ty, tz, nb);
                 if ((s.mask >> lane) & 1u) {
-                    if (atomicExch(&B.astamp[tb], step + 1) != step + 1)
-                        act_next[atomicAdd(&ctrl->nactive[par ^ 1], 1u)] = tb;
+                    // heavy: b itself (lane 13) with more than kHeavy particles now.  A
+                    // neighbour's mark wins only for blocks that particles enter from
+                    // outside, which are light.
+                    if (atomicExch(&B.astamp[tb], step + 1) != step + 1) {
+                        if (lane == 13 && s.total > kHeavy)
+                            act_next[atomicAdd(&ctrl->nactive[par ^ 1][0], 1u)] = tb;
+                        else
+                            act_next[acap - 1u - atomicAdd(&ctrl->nactive[par ^ 1][1], 1u)] = tb;
+                    }
                 }
                 mark_clear(B, tb, step + 1, m3n);
             }
@@ -722,7 +737,8 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
             ctrl->work = 0;
             ctrl->part_alloc = 0;
             ctrl->chunk_alloc = 0;
-            ctrl->nactive[par] = 0;
+            ctrl->nactive[par][0] = 0;
+            ctrl->nactive[par][1] = 0;
             ctrl->nclear[m3c] = 0;
             ctrl->done = 0;
             __threadfence();

@@ -204,7 +204,7 @@ __global__ void k_init_tables(DevParams P, const uint32_t *__restrict__ offsets,
         for (int d = 0; d < 27; ++d) ch.run[d] = make_uint2(d == 13 ? off : 0u, d == 13 ? c : 0u);
         B.inbox[par][(size_t)b * kInbox + 13 * kNpMax] = make_uint4(off, c, step, 0u);
         B.astamp[b] = step;
-        B.alist[par][atomicAdd(&B.ctrl->nactive[par], 1u)] = b;
+        B.alist[par][atomicAdd(&B.ctrl->nactive[par][0], 1u)] = b;
         const uint32_t e = b / P.nbe, bl = b % P.nbe;
         const int bx = bl % P.nb, by = (bl / P.nb) % P.nb, bz = bl / (P.nb * P.nb);
         for (int d = 0; d < 27; ++d) {
