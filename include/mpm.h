@@ -256,16 +256,19 @@ mpm_status mpm_extract_surface(mpm_handle *h, int32_t env, float iso, float *tri
 /* ------------------------------------------------------------ kernel tuning */
 
 /* Configurations of the fused sub-step kernel: CTA size x passes of particles
- * staged per shared-memory P2G flush.  More, smaller CTAs waste fewer threads
- * on sparsely filled grid blocks (small or batched scenes); larger CTAs and
- * groups amortise the per-block work on dense blocks.  Not in the paper (its
+ * staged per shared-memory P2G flush (x resident CTAs per SM).  More, smaller
+ * CTAs waste fewer threads on sparsely filled grid blocks (small or batched
+ * scenes); larger CTAs and groups amortise the per-block work on dense
+ * blocks; two CTAs per SM with twice the registers shorten the latency chain
+ * of a block when there are few blocks per CTA.  Not in the paper (its
  * Taichi kernels are tuned by Taichi); a utility of this library. */
 enum {
     MPM_KERNEL_T256_G2 = 0, /* 256 threads, 512 particles per flush (the default) */
     MPM_KERNEL_T256_G1 = 1, /* 256 threads, 256 particles per flush */
     MPM_KERNEL_T128_G2 = 2, /* 128 threads, 256 particles per flush */
     MPM_KERNEL_T128_G1 = 3, /* 128 threads, 128 particles per flush */
-    MPM_KERNEL_CONFIGS = 4
+    MPM_KERNEL_T256_G2_C2 = 4, /* 256 threads, 512 particles per flush, 2 CTAs per SM */
+    MPM_KERNEL_CONFIGS = 5
 };
 
 /* Select the fused kernel configuration (fused pipeline; the split pipeline

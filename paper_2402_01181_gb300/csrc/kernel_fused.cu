@@ -176,8 +176,9 @@ __device__ __forceinline__ void prefetch_block(Smem &s, int buf, uint32_t b, con
 }
 
 
-template <bool WRITE_VC, int T, int GP>
-__global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P, FusedBufs B,
+// MINB: resident CTAs per SM the configuration is compiled for (the register budget)
+template <bool WRITE_VC, int T, int GP, int MINB = kMinBlocks<T, GP>>
+__global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B,
                                                                      const ToolFrame *__restrict__ tools) {
     using Smem = FusedSmem<T, GP>;
     constexpr int NW = Smem::NW, GROUP = Smem::GROUP;
@@ -747,23 +748,23 @@ __global__ void __launch_bounds__(T, kMinBlocks<T, GP>) k_fused_step(DevParams P
     }
 }
 
-template <int T, int GP>
+template <int T, int GP, int MINB = kMinBlocks<T, GP>>
 void launch_variant(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, bool write_vc, int grid,
                     cudaStream_t st) {
     if (write_vc)
-        k_fused_step<true, T, GP><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools);
+        k_fused_step<true, T, GP, MINB><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools);
     else
-        k_fused_step<false, T, GP><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools);
+        k_fused_step<false, T, GP, MINB><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools);
 }
 
-template <int T, int GP>
+template <int T, int GP, int MINB = kMinBlocks<T, GP>>
 int variant_occupancy() {
     const int bytes = (int)sizeof(FusedSmem<T, GP>);
-    cudaFuncSetAttribute(k_fused_step<true, T, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_fused_step<false, T, GP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_fused_step<true, T, GP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_fused_step<false, T, GP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fused_step<true, T, GP>, T, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_step<false, T, GP>, T, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fused_step<true, T, GP, MINB>, T, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_step<false, T, GP, MINB>, T, bytes);
     return a < b ? a : b;
 }
 
@@ -775,11 +776,12 @@ void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *
     case 1: launch_variant<256, 1>(P, B, tools, write_vc, grid, st); break;
     case 2: launch_variant<128, 2>(P, B, tools, write_vc, grid, st); break;
     case 3: launch_variant<128, 1>(P, B, tools, write_vc, grid, st); break;
+    case 4: launch_variant<256, 2, 2>(P, B, tools, write_vc, grid, st); break;   // 2 CTAs per SM, 128 registers
     default: launch_variant<256, 2>(P, B, tools, write_vc, grid, st); break;
     }
 }
 
-int fused_step_threads(int config) { return config >= 2 ? 128 : 256; }
+int fused_step_threads(int config) { return config == 2 || config == 3 ? 128 : 256; }
 
 // Also opts the kernel into its dynamic shared memory size on the current
 // device; called when a handle is created.
@@ -788,6 +790,7 @@ int fused_step_occupancy(int config) {
     case 1: return variant_occupancy<256, 1>();
     case 2: return variant_occupancy<128, 2>();
     case 3: return variant_occupancy<128, 1>();
+    case 4: return variant_occupancy<256, 2, 2>();
     default: return variant_occupancy<256, 2>();
     }
 }

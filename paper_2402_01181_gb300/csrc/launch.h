@@ -100,7 +100,7 @@ void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *
                        int config, cudaStream_t st);
 int fused_step_occupancy(int config);
 int fused_step_threads(int config);
-constexpr int kFusedConfigs = 4;
+constexpr int kFusedConfigs = 5;
 constexpr int kFusedMinThreads = 128;     // chunk tables are sized for the smallest CTA
 // Inbox of a block: entry d * kNpMax + p holds the run of source pass p
 // coming from direction d (source block = block - dir(d)); the last entry,

@@ -35,9 +35,10 @@ MPM_TOOL_CAPSULE = 0
 MPM_TOOL_BOX = 1
 MPM_TOOL_SAMPLED = 2
 MPM_MAX_FIELDS = 16
-MPM_KERNEL_CONFIGS = 4
+MPM_KERNEL_CONFIGS = 5
 KERNEL_CONFIG_NAMES = {0: "256 threads, 2 passes per flush", 1: "256 threads, 1 pass per flush",
-                       2: "128 threads, 2 passes per flush", 3: "128 threads, 1 pass per flush"}
+                       2: "128 threads, 2 passes per flush", 3: "128 threads, 1 pass per flush",
+                       4: "256 threads, 2 passes per flush, 2 CTAs per SM"}
 MPM_MAX_FIELD_RES = 1024
 
 STATUS_NAMES = {0: "MPM_OK", -1: "MPM_ERR_ARG", -2: "MPM_ERR_ALLOC", -3: "MPM_ERR_CUDA", -4: "MPM_ERR_NUMERIC",

@@ -11,7 +11,7 @@ from paper_2402_01181_gb300 import scenes
 
 pytestmark = pytest.mark.gpu
 
-CONFIGS = [0, 1, 2, 3]
+CONFIGS = [0, 1, 2, 3, 4]
 
 
 @pytest.fixture(scope="module")
