@@ -43,7 +43,6 @@ namespace gbmpm {
 namespace {
 
 constexpr int CMAX = 512;      // run candidates (source chunk x direction) per block
-constexpr uint32_t kHeavy = 256;        // particles above which a block's item is listed first
 constexpr float kFix = 4194304.0f;      // 2^22
 constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23: float -> nearest int for |v| < 2^22
 // arena node (x, y, z) in [0,8)^3 sits at x + kAy y + kAz z: kAz = 68 keeps the
@@ -711,11 +710,11 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
             if (tx >= 0 && ty >= 0 && tz >= 0 && tx < nb && ty < nb && tz < nb) {
                 const uint32_t tb = eb0 + block_id(tx, ty, tz, nb);
                 if ((s.mask >> lane) & 1u) {
-                    // heavy: b itself (lane 13) with more than kHeavy particles now.  A
-                    // neighbour's mark wins only for blocks that particles enter from
-                    // outside, which are light.
+                    // heavy: b itself (lane 13) with more particles now than one pass
+                    // of the CTA takes.  A neighbour's mark wins only for blocks that
+                    // particles enter from outside, which are light.
                     if (atomicExch(&B.astamp[tb], step + 1) != step + 1) {
-                        if (lane == 13 && s.total > kHeavy)
+                        if (lane == 13 && s.total > (uint32_t)T)
                             act_next[atomicAdd(&ctrl->nactive[par ^ 1][0], 1u)] = tb;
                         else
                             act_next[acap - 1u - atomicAdd(&ctrl->nactive[par ^ 1][1], 1u)] = tb;
