@@ -121,3 +121,42 @@ def test_batch_sort_order(M):
         sim.step(1)
         ids, keys = sim.read_order()
     sim.close()
+
+
+def test_batch256_full_size_sampled_envs_match_oracle(M):
+    """The benchmark's batched workload at full size (256 slab environments of
+    5K-40K particles on their own 64^3 grids), autotuned as the benchmark runs
+    it: after one 25-sub-step frame with every tool moving, one more sub-step
+    of eight sampled environments matches the oracle from the same state."""
+    envs = scenes.batch_envs(256, seed=0)
+    S = 25
+    cfg = M.make_config(64, envs[0].dt, 1e4, 0.3, 1e3, friction=0.3, n_envs=len(envs),
+                        max_particles=sum(e.n for e in envs))
+    sim = M.Sim(cfg)
+    for i, sc in enumerate(envs):
+        sim.set_env_material(i, sc.E, sc.nu, sc.rho)
+    sim.load_batch([sc.x for sc in envs], [sc.particle_volume for sc in envs])
+    for i, sc in enumerate(envs):
+        sim.set_env_tool(i, 0, sc.tools[0].pose(-1), sc.tools[0].shape)
+    best, _ = sim.autotune(S)
+    assert sim.kernel_config()["config"] == best
+    for i, sc in enumerate(envs):
+        sim.set_env_tool(i, 0, sc.tools[0].pose(S - 1), sc.tools[0].shape)
+    sim.step(S)
+    start = _split(sim.read(), envs)
+    for i, sc in enumerate(envs):
+        sim.set_env_tool(i, 0, sc.tools[0].pose(S), sc.tools[0].shape)
+    sim.step(1)
+    out = _split(sim.read(), envs)
+    assert sim.status() == M.MPM_OK
+    sim.close()
+    for e in (0, 37, 74, 111, 148, 185, 222, 255):
+        sc = envs[e]
+        st = H.oracle_state(start[e])
+        mask = H.contact_mask_nodes(sc, st, S)
+        skip = H.particles_touching(mask, st.x, sc.n_grid)
+        frames, nt = O.frames_for_steps(sc.tools, S, 1, sc.dt, 1)
+        O.run(O.OracleParams.from_scene(sc), st, 1, frames, nt)
+        ok, errs = H.compare_particles(out[e], st, sc.dx, skip)
+        assert ok, (e, errs)
+        assert mask.sum() <= 5, e
