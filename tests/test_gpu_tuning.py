@@ -128,3 +128,38 @@ def test_autotune_picks_a_config_and_restores_the_state(M):
     ref.close()
     dxp = np.abs(tuned["x"] - base["x"]).max(axis=1)
     assert np.quantile(dxp, 0.99) <= 1e-4 * sc.dx and dxp.max() <= 1e-2 * sc.dx
+
+
+@pytest.mark.parametrize("config", CONFIGS)
+def test_particles_moving_more_than_a_cell_scatter_directly(M, config):
+    """A lattice block moving 1.8, 0.6 and -1.2 cells per sub-step along x,
+    y, z: after one sub-step the particles near its +x and -z faces have base
+    cells outside the 8^3 shared arena of their block, so their P2G goes
+    straight into G_{k+1} with float atomics.  The grid the next sub-step
+    starts from matches the oracle's P2G of the GPU's own new state, and so
+    does the next sub-step."""
+    n, dt = 32, 1e-4
+    x = scenes.jittered_lattice((8, 8, 8), (16, 16, 16), n, (2, 2, 2), seed=9)
+    cell_per_step = np.array([1.8, 0.6, -1.2]) / n / dt
+    v = np.tile(cell_per_step, (x.shape[0], 1)).astype(np.float32)
+    sc = scenes.Scene("fast", n_grid=n, dt=dt, E=50.0, nu=0.3, rho=1e3, x=x, particle_volume=(1.0 / n) ** 3 / 8, v=v)
+    sim = M.sim_from_scene(sc)
+    sim.set_kernel_config(config)
+    sim.step(1)
+    g = sim.read_grid().astype(np.float64)
+    out = sim.read()
+    st = H.oracle_state(out)
+    # some particles did leave their block's arena: base cell more than one cell past the block
+    base = np.floor(st.x * n - 0.5).astype(int)
+    blk_before = np.floor(sc.x * n - 0.5).astype(int) // 4
+    assert ((base[:, 0] - 4 * blk_before[:, 0] > 4) | (base[:, 2] - 4 * blk_before[:, 2] < -1)).sum() > 100
+    gm, gmv = O.p2g(O.OracleParams.from_scene(sc), st.copy())
+    assert H.rel_err(g[..., 0], gm) <= 1e-5
+    assert H.rel_err(g[..., 1:], gmv) <= 1e-5
+    sim.step(1)
+    out2 = sim.read()
+    assert sim.status() == M.MPM_OK
+    sim.close()
+    H.oracle_steps(sc, st, 1, 1)
+    ok, errs = H.compare_particles(out2, st, sc.dx)
+    assert ok, (config, errs)
