@@ -54,3 +54,12 @@ def test_oracle_timer_reports_a_bounded_sample():
     O.build()
     rate, sample = bench.time_oracle("cube8k", 2.0, max_steps=2)
     assert rate > 0 and "cube8k" in sample and sample.startswith(("1 ", "2 "))
+
+
+def test_counter_record_hash_ignores_comments_only():
+    a = "int f(int x) {  // one\n    return x + 1; /* two */\n}\n"
+    b = "// header\nint f(int x) {\n\n    return   x + 1;\n}\n"
+    c = "int f(int x) {\n    return x + 2;\n}\n"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
+    assert len(bench.kernel_source_sha()) == 16
