@@ -62,6 +62,9 @@ MUTATIONS = {
     "surface quad parity ignored": ("if (inv & 1) { const int x = perm[2];", "if (0) { const int x = perm[2];"),
     "surface interpolation from the wrong end": ("const double t = (iso - f[a]) / (f[b] - f[a]);",
                                                  "const double t = (f[b] - iso) / (f[b] - f[a]);"),
+    "wall band one node narrower at the top": ("i >= n - b || j >= n - b || k >= n - b;", "i > n - b || j > n - b || k > n - b;"),
+    "friction with the wrong sign": ("c->s = c->vtn + p->friction * c->vn;", "c->s = c->vtn - p->friction * c->vn;"),
+    "Lame lambda with 1 + 2 nu": ("*lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));", "*lam = E * nu / ((1.0 + nu) * (1.0 + 2.0 * nu));"),
     "block key axis order": ("keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));", "keys[q] = (uint32_t)(b[2] + nb * (b[1] + nb * b[0]));"),
 }
 

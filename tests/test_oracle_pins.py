@@ -610,3 +610,22 @@ def test_sampled_capsule_agrees_with_the_analytic_capsule():
             far += 1
             assert ca[i, j, k] == cs[i, j, k], (i, j, k, da)
     assert far > 1000 and (ca == 0).sum() > 50
+
+
+def test_wall_band_is_three_nodes_deep_on_every_face():
+    """Sec. III-B boundary condition, reading c4: sticky walls zero the velocity
+    of every node within 3 nodes of any face.  Checked by closed forms rather
+    than by the band test itself: the zeroed set holds n^3 - (n - 6)^3 nodes,
+    it is mirror-symmetric on every axis (node i <-> n - 1 - i, the domain
+    [0, 1) seen from either end), and no interior node is touched."""
+    n = 16
+    prm = O.OracleParams(n_grid=n, dt=1e-3, E=1e3, nu=0.3, rho=1e3, V0=1e-6, gravity=(0.0, 0.0, 0.0))
+    gm = np.ones(n ** 3)
+    gmv = np.tile([1.0, 2.0, 3.0], n ** 3)
+    v, _, _ = O.grid_update(prm, gm, gmv)
+    zero = np.all(v == 0.0, axis=-1)
+    assert zero.sum() == n ** 3 - (n - 6) ** 3
+    for ax in range(3):
+        assert np.array_equal(zero, np.flip(zero, axis=ax))
+    assert not zero[3:n - 3, 3:n - 3, 3:n - 3].any()
+    assert np.allclose(v[~zero], [1.0, 2.0, 3.0])
