@@ -65,6 +65,10 @@ MUTATIONS = {
     "wall band one node narrower at the top": ("i >= n - b || j >= n - b || k >= n - b;", "i > n - b || j > n - b || k > n - b;"),
     "friction with the wrong sign": ("c->s = c->vtn + p->friction * c->vn;", "c->s = c->vtn - p->friction * c->vn;"),
     "Lame lambda with 1 + 2 nu": ("*lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));", "*lam = E * nu / ((1.0 + nu) * (1.0 + 2.0 * nu));"),
+    "C scaled by 3 / dx^2": ("Cp[a] = 4.0 / (dx * dx) * B[a];     /* Eq. 9 */", "Cp[a] = 3.0 / (dx * dx) * B[a];     /* Eq. 9 */"),
+    "stencil base without the half-cell shift": ("int b = (int)floor(s - 0.5);\n        if (b < 0) { b = 0; bad = 1; }",
+                                                 "int b = (int)floor(s);\n        if (b < 0) { b = 0; bad = 1; }"),
+    "volumetric stress term dropped": ("P[i] = mu * (F[i] - FiT[i]) + lam * lnJ * FiT[i];", "P[i] = mu * (F[i] - FiT[i]);"),
     "block key axis order": ("keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));", "keys[q] = (uint32_t)(b[2] + nb * (b[1] + nb * b[0]));"),
 }
 
