@@ -69,6 +69,11 @@ MUTATIONS = {
     "stencil base without the half-cell shift": ("int b = (int)floor(s - 0.5);\n        if (b < 0) { b = 0; bad = 1; }",
                                                  "int b = (int)floor(s);\n        if (b < 0) { b = 0; bad = 1; }"),
     "volumetric stress term dropped": ("P[i] = mu * (F[i] - FiT[i]) + lam * lnJ * FiT[i];", "P[i] = mu * (F[i] - FiT[i]);"),
+    "empty nodes get gravity": ("                if (grid_m[I] > 0.0) {\n                    for (int a = 0; a < 3; ++a)",
+                                "                if (grid_m[I] >= 0.0) {\n                    for (int a = 0; a < 3; ++a)"),
+    "particle mass without density": ("    const double dx = 1.0 / n;\n    const double mp = p->rho * p->V0;",
+                                      "    const double dx = 1.0 / n;\n    const double mp = p->V0;"),
+    "z-buffer tie goes to the later tool": ("        if (d < dmin) {\n            *d2 = dmin;", "        if (d <= dmin) {\n            *d2 = dmin;"),
     "block key axis order": ("keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));", "keys[q] = (uint32_t)(b[2] + nb * (b[1] + nb * b[0]));"),
 }
 

@@ -629,3 +629,28 @@ def test_wall_band_is_three_nodes_deep_on_every_face():
         assert np.array_equal(zero, np.flip(zero, axis=ax))
     assert not zero[3:n - 3, 3:n - 3, 3:n - 3].any()
     assert np.allclose(v[~zero], [1.0, 2.0, 3.0])
+
+
+def test_zbuffer_tie_goes_to_the_lower_tool_index():
+    """Sec. III-C's multi-object merge, reading c11: on a tie of the closest
+    distance, the lower object index wins.  Two capsules at the same pose with
+    different velocities tie at every node; the pair must act exactly as the
+    first capsule alone, and not as the second."""
+    rng = np.random.default_rng(21)
+    prm = _params(n=16, friction=0.3)
+    n = prm.n_grid
+    m = np.zeros((n, n, n))
+    mv = np.zeros((n, n, n, 3))
+    m[4:12, 4:12, 4:12] = 1.0 + rng.random((8, 8, 8))
+    mv[4:12, 4:12, 4:12] = rng.normal(size=(8, 8, 8, 3))
+    base = {"shape": [scenes.CAPSULE, 0.12, 0.1, 0.0], "T": [0.5, 0.52, 0.48], "w": [0.0, 0.0, 0.0],
+            "R": list(O.rotvec_to_matrix(np.array([0.3, -0.2, 0.4])).reshape(9))}
+    t0 = dict(base, u=[0.4, -1.0, 0.2])
+    t1 = dict(base, u=[-0.7, 0.5, 0.9])
+    v01, c01, _ = O.grid_update(prm, m, mv, _frames_from_case([t0, t1]), 2)
+    v0, c0, _ = O.grid_update(prm, m, mv, _frames_from_case([t0]), 1)
+    v1, _, _ = O.grid_update(prm, m, mv, _frames_from_case([t1]), 1)
+    hit = c0 == 0
+    assert hit.sum() > 20
+    assert np.array_equal(v01, v0) and np.array_equal(c01, c0)
+    assert np.abs(v01[hit] - v1[hit]).max() > 0.1
