@@ -74,6 +74,10 @@ MUTATIONS = {
     "particle mass without density": ("    const double dx = 1.0 / n;\n    const double mp = p->rho * p->V0;",
                                       "    const double dx = 1.0 / n;\n    const double mp = p->V0;"),
     "z-buffer tie goes to the later tool": ("        if (d < dmin) {\n            *d2 = dmin;", "        if (d <= dmin) {\n            *d2 = dmin;"),
+    "tool velocity over one sub-step, not the call": ("t->u[d] = (pose1[d] - pose0[d]) / span;", "t->u[d] = (pose1[d] - pose0[d]) / dt;"),
+    "tool poses not interpolated within a call": ("t->T[d] = pose0[d] + s * (pose1[d] - pose0[d]);", "t->T[d] = pose1[d];"),
+    "box interior normal on the wrong axis": ("    if (q[1] > q[a]) a = 1;\n    if (q[2] > q[a]) a = 2;", "    if (q[1] < q[a]) a = 1;\n    if (q[2] < q[a]) a = 2;"),
+    "capsule segment not clamped": ("        if (c > dims[1]) c = dims[1];\n", ""),
     "block key axis order": ("keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));", "keys[q] = (uint32_t)(b[2] + nb * (b[1] + nb * b[0]));"),
 }
 

@@ -451,6 +451,14 @@ def test_rotation_maps_and_tool_frames():
     R0 = np.array(fr[1].R).reshape(3, 3)
     R1 = np.array(fr[2].R).reshape(3, 3)
     assert np.allclose(O.matrix_to_rotvec(R1 @ R0.T) / dt, np.array(fr[0].w), atol=1e-9)
+    # kinematic consistency inside the call: every sub-step's pose moves on from
+    # the previous one (from pose0 for the first) by the frame's own velocities
+    prevT, prevR = p0[:3], O.rotvec_to_matrix(p0[3:])
+    for k in range(nsub):
+        Tk, Rk = np.array(fr[k].T), np.array(fr[k].R).reshape(3, 3)
+        assert np.allclose(Tk - prevT, np.array(fr[k].u) * dt, atol=1e-15), k
+        assert np.allclose(O.matrix_to_rotvec(Rk @ prevR.T), np.array(fr[k].w) * dt, atol=1e-12), k
+        prevT, prevR = Tk, Rk
 
 
 # --------------------------------------------------------------- sort keys
