@@ -143,3 +143,32 @@ def test_rollout_gradients_match_central_differences():
         fd = (loss(prm, pa) - loss(prm, pb)) / (2 * h)
         an = g["poses"][k, t, c]
         assert abs(fd - an) <= 1e-4 * max(abs(fd), 1e-6 * np.abs(g["poses"]).max()), ((k, t, c), fd, an)
+
+
+@pytest.mark.parametrize("block", ["x", "v"])
+def test_step_adjoint_near_the_walls_matches_central_differences(block):
+    """Particles resting near the floor and a side wall, whose stencils reach
+    the sticky band of the grid operation (Sec. III-B, reading c4): the
+    forward step zeroes those nodes' velocities, so nothing flows back
+    through them, and the adjoint must agree with central differences."""
+    rng = np.random.default_rng(8)
+    N, n, dt = 200, 16, 1e-3
+    x = np.stack([0.06 + 0.3 * rng.random(N), 0.07 + 0.3 * rng.random(N), 0.3 + 0.4 * rng.random(N)], axis=1)
+    v, C, F = scenes.random_state(x.astype(np.float32), 9, v_scale=0.4, c_scale=1.5, f_dev=0.12)
+    prm = O.OracleParams(n_grid=n, dt=dt, E=3e3, nu=0.32, rho=1e3, V0=(0.3 ** 3) / N, bound=3,
+                         gravity=(0.0, -9.8, 0.0))
+    st = O.State(x, v.astype(np.float64), C.astype(np.float64), F.astype(np.float64))
+    frames = (O.ToolFrame * 1)()
+    base = np.floor(x * n - 0.5).astype(int)
+    assert (base.min(axis=1) < 3).sum() > 50                  # stencils inside the wall band
+    ybar = _random_bar(rng, N)
+    xbar, _, _ = O.step_adjoint(prm, st, frames, 0, ybar)
+    h = 1e-6 if block == "x" else 1e-5
+    for trial in range(3):
+        d = rng.normal(size=getattr(st, block).shape)
+        a, b = st.copy(), st.copy()
+        getattr(a, block)[...] += h * d
+        getattr(b, block)[...] -= h * d
+        fd = (_dot(ybar, _step(prm, a, frames, 0)) - _dot(ybar, _step(prm, b, frames, 0))) / (2 * h)
+        an = float(np.sum(xbar[block] * d))
+        assert abs(fd - an) <= 1e-5 * abs(fd), (block, trial, fd, an)

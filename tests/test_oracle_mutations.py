@@ -78,6 +78,8 @@ MUTATIONS = {
     "tool poses not interpolated within a call": ("t->T[d] = pose0[d] + s * (pose1[d] - pose0[d]);", "t->T[d] = pose1[d];"),
     "box interior normal on the wrong axis": ("    if (q[1] > q[a]) a = 1;\n    if (q[2] > q[a]) a = 2;", "    if (q[1] < q[a]) a = 1;\n    if (q[2] < q[a]) a = 2;"),
     "capsule segment not clamped": ("        if (c > dims[1]) c = dims[1];\n", ""),
+    "adjoint flows through the walls": ("                if (in_wall_band(p, i, j, k)) continue;\n                double vf[3], vbar[3];",
+                                        "                double vf[3], vbar[3];"),
     "block key axis order": ("keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));", "keys[q] = (uint32_t)(b[2] + nb * (b[1] + nb * b[0]));"),
 }
 
