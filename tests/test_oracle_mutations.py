@@ -80,6 +80,10 @@ MUTATIONS = {
     "capsule segment not clamped": ("        if (c > dims[1]) c = dims[1];\n", ""),
     "adjoint flows through the walls": ("                if (in_wall_band(p, i, j, k)) continue;\n                double vf[3], vbar[3];",
                                         "                double vf[3], vbar[3];"),
+    "surface skips the last cell layer": ("    for (int k = 0; k + 1 < n; ++k)\n        for (int j = 0; j + 1 < n; ++j)",
+                                          "    for (int k = 0; k + 2 < n; ++k)\n        for (int j = 0; j + 1 < n; ++j)"),
+    "surface tetrahedron orientation ignored": ("if (tet_orientation(t[0], t[1], t[2], t[3]) < 0) {", "if (0) {"),
+    "surface nin = 3 winding not flipped": ("if (nin == 3) { int s0 = e[1][0]", "if (0) { int s0 = e[1][0]"),
     "block key axis order": ("keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));", "keys[q] = (uint32_t)(b[2] + nb * (b[1] + nb * b[0]));"),
 }
 
