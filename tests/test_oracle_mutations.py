@@ -84,6 +84,10 @@ MUTATIONS = {
                                           "    for (int k = 0; k + 2 < n; ++k)\n        for (int j = 0; j + 1 < n; ++j)"),
     "surface tetrahedron orientation ignored": ("if (tet_orientation(t[0], t[1], t[2], t[3]) < 0) {", "if (0) {"),
     "surface nin = 3 winding not flipped": ("if (nin == 3) { int s0 = e[1][0]", "if (0) { int s0 = e[1][0]"),
+    "tool contact at cell centres, not nodes": ("const double xw[3] = {i * dx, j * dx, k * dx};\n                        double nref[3]",
+                                                "const double xw[3] = {(i + 0.5) * dx, (j + 0.5) * dx, (k + 0.5) * dx};\n                        double nref[3]"),
+    "gravity added to momentum before the division": ("v[a] = grid_mv[3 * I + a] / grid_m[I] + p->dt * p->gravity[a];  /* Eq. 7 + gravity */",
+                                                      "v[a] = (grid_mv[3 * I + a] + p->dt * p->gravity[a]) / grid_m[I];  /* Eq. 7 + gravity */"),
     "block key axis order": ("keys[q] = (uint32_t)(b[0] + nb * (b[1] + nb * b[2]));", "keys[q] = (uint32_t)(b[2] + nb * (b[1] + nb * b[0]));"),
 }
 
