@@ -532,6 +532,38 @@ def run_surface(args, rank, device, barrier, max_over_ranks, reps=10):
             "achieved_gbs": algo / (ms / 1e3) / 1e9, "note": "median of %d; includes one 4-byte readback" % reps}
 
 
+def survey_bytes_per_particle_step(n, active_nodes):
+    """Algorithmic DRAM traffic per particle-step of the method as the
+    benchmark plan states it: the persistent FP32 state x, v, A, F (24 floats,
+    96 B) read once and written once (192 B), plus 72 B per active grid node
+    (clear 16, P2G result 16, grid read 16, velocity write 12, G2P read 12)."""
+    return 192.0 + 72.0 * active_nodes / n
+
+
+def cpu_description():
+    """CPU model and the number of online cores of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for ln in fh:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    import platform
+    return {"cpu_model": model or platform.machine(), "nproc": os.cpu_count(), "arch": platform.machine()}
+
+
 def algorithmic_bytes_per_particle_step(n, active_nodes, S):
     """Minimum DRAM traffic of one fused sub-step, per particle: the particle
     state is read and written once (x, id: 16 B; F: 36 B; twice = 104 B); each
@@ -581,7 +613,7 @@ def reference_main(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "impl": "FP64 single-threaded C oracle"},
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, **cpu_description()},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -637,9 +669,11 @@ def main():
         return
 
     peak, peak_kind = measured_peak()
-    bpp = algorithmic_bytes_per_particle_step(main_res["n"], main_res["active_nodes"], S)
+    bpp_design = algorithmic_bytes_per_particle_step(main_res["n"], main_res["active_nodes"], S)
+    bpp = survey_bytes_per_particle_step(main_res["n"], main_res["active_nodes"])
     launch_ms = main_res["t_ms"] / (args.steps * S)      # per fused launch (frame time / sub-steps)
     achieved = bpp * main_res["n"] / (launch_ms / 1e3) / 1e9
+    achieved_design = bpp_design * main_res["n"] / (launch_ms / 1e3) / 1e9
     traffic = None
     counts = None
     try:
@@ -654,7 +688,12 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_fused_step" if args.pipeline == "fused"
                 else "p2g+grid+g2p", "algorithmic_bytes_per_particle_step": bpp,
-                "launch_us": launch_ms * 1e3}
+                "basis": "benchmark plan: x, v, A, F read and written once (192 B) + 72 B per active grid node",
+                "launch_us": launch_ms * 1e3,
+                "fused_design_basis": {"algorithmic_bytes_per_particle_step": bpp_design,
+                                       "achieved": achieved_design, "frac": achieved_design / peak,
+                                       "basis": "state the fused kernel keeps: x, id, F read and written once "
+                                                "(104 B) + 48 B per active node + v, C once per call"}}
     # the CUDA-core side: FP32 FLOPs and thread instructions per particle-step
     # from the ncu capture of this kernel, against the rates of this GPU at the
     # sampled maximum SM clock (128 FP32 lanes and 4 x 32 issue lanes per SM)
@@ -677,7 +716,8 @@ def main():
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, sample = time_oracle(args.workload, 15.0)
-        cpu = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample,
+               **cpu_description()}
     e2e_val = main_res["n"] * S * args.steps * world / (main_res["t_e2e_ms"] / 1e3)
     launches_per_frame = S if args.pipeline == "fused" else 3 * S
     line = {

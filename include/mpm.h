@@ -339,14 +339,19 @@ mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_b
  * in [8, 256]; n <= 2^30; larger sizes return MPM_ERR_ARG.
  *
  * Allocates nothing: its scratch is one static device array of about 3 MB
- * that every GPU using the library holds until the process exits.  The first
- * call on a device looks up that array's address (cudaGetSymbolAddress, with
- * the device current), so make it before any stream capture.  Every call
+ * that every GPU using the library holds until the process exits.  Every
+ * call looks up that array's address in the current context
+ * (cudaGetSymbolAddress, with the device current), so a host driving the GPU
+ * through its own context, or one that has reset the device, gets the right
+ * copy; the first call in a context also loads the library's device code
+ * there, so make that first call before any stream capture.  Every call
  * shares the array and leaves its contents behind (the counters are cleared
  * at the start of each call); calls that overlap on the GPU, on any streams,
  * race and must not be issued.  Runs on cuda_stream (NULL = legacy default)
- * and synchronises it; returns MPM_ERR_NUMERIC / MPM_ERR_DOMAIN for
- * non-finite or clamped positions. */
+ * and blocks the calling thread until that work is done; returns
+ * MPM_ERR_NUMERIC / MPM_ERR_DOMAIN for non-finite or clamped positions (the
+ * outputs then hold the order of the clamped keys, and the next call starts
+ * clean). */
 mpm_status mpm_block_sort_noalloc(const float *x, int64_t n, int32_t n_grid, uint32_t *ids,
                                   uint32_t *keys, void *cuda_stream);
 

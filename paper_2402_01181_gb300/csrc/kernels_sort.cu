@@ -3,7 +3,8 @@
 // particle: the block containing its stencil base floor(x/dx - 0.5); ties
 // keep particle-index order.  Steps: key + histogram, exclusive scan, atomic
 // scatter, per-block sort of the (distinct) particle indices so that every
-// block lists its particles in index order.
+// block lists its particles in index order (the keys array is reused as
+// scratch by that last step).
 #include "common.cuh"
 #include "launch.h"
 
@@ -95,21 +96,27 @@ __global__ void k_scatter_ids(const uint32_t *__restrict__ keys, uint32_t n, uin
         perm[atomicAdd(&cursor[keys[p]], 1u)] = p;
 }
 
-// Restore index order inside every block's segment of perm.
+// Restore index order inside every block's segment of perm (the ids of one
+// segment are distinct).  Every chunk of up to kSegSortMax ids is sorted in
+// shared memory (bitonic network); a longer segment then merges its sorted
+// chunks pairwise, doubling the run length per pass: each id finds its output
+// position as its rank in its own run plus the number of smaller ids in the
+// partner run (a binary search).  The passes alternate between the segment in
+// perm and the same slot range of tmp, so the work is O(c log^2 c) for a
+// segment of c ids and no segment reads another's ids.
 constexpr int kSegSortMax = 2048;
-__global__ void __launch_bounds__(256) k_segment_sort(const uint32_t *__restrict__ offsets,
-                                                      const uint32_t *__restrict__ keys, uint32_t n, uint32_t m,
-                                                      uint32_t *__restrict__ perm) {
+__global__ void __launch_bounds__(256) k_segment_sort(const uint32_t *__restrict__ offsets, uint32_t m,
+                                                      uint32_t *__restrict__ perm, uint32_t *__restrict__ tmp) {
     __shared__ uint32_t s[kSegSortMax];
-    __shared__ uint32_t s_wc[8];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     for (uint32_t b = blockIdx.x; b < m; b += gridDim.x) {
         const uint32_t off = offsets[b], c = offsets[b + 1] - off;
         if (c <= 1) continue;
-        if (c <= kSegSortMax) {
+        for (uint32_t c0 = 0; c0 < c; c0 += kSegSortMax) {
+            const uint32_t cc = min((uint32_t)kSegSortMax, c - c0);
             uint32_t L = 2;
-            while (L < c) L <<= 1;
-            for (uint32_t i = tid; i < L; i += blockDim.x) s[i] = i < c ? perm[off + i] : 0xffffffffu;
+            while (L < cc) L <<= 1;
+            for (uint32_t i = tid; i < L; i += blockDim.x) s[i] = i < cc ? perm[off + c0 + i] : 0xffffffffu;
             __syncthreads();
             for (uint32_t k = 2; k <= L; k <<= 1) {
                 for (uint32_t j = k >> 1; j > 0; j >>= 1) {
@@ -124,26 +131,32 @@ __global__ void __launch_bounds__(256) k_segment_sort(const uint32_t *__restrict
                     __syncthreads();
                 }
             }
-            for (uint32_t i = tid; i < c; i += blockDim.x) perm[off + i] = s[i];
+            for (uint32_t i = tid; i < cc; i += blockDim.x) perm[off + c0 + i] = s[i];
             __syncthreads();
-        } else {
-            // large segment: stable compaction of all particles with this key
-            uint32_t written = 0;
-            for (uint32_t t0 = 0; t0 < n; t0 += blockDim.x) {
-                const uint32_t p = t0 + tid;
-                const bool hit = p < n && keys[p] == b;
-                const unsigned bal = __ballot_sync(0xffffffffu, hit);
-                if (lane == 0) s_wc[warp] = __popc(bal);
-                __syncthreads();
-                uint32_t before = 0, total = 0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                    if (w < warp) before += s_wc[w];
-                    total += s_wc[w];
+        }
+        if (c <= (uint32_t)kSegSortMax) continue;
+        uint32_t *src = perm + off, *dst = tmp + off;
+        for (uint32_t w = kSegSortMax; w < c; w <<= 1) {
+            for (uint32_t i = tid; i < c; i += blockDim.x) {
+                const uint32_t r0 = i / (2 * w) * (2 * w);
+                const uint32_t mid = min(r0 + w, c), end = min(r0 + 2 * w, c);
+                const uint32_t v = src[i];
+                const bool in_a = i < mid;
+                // partner run [lo, hi): count its ids smaller than v
+                uint32_t lo = in_a ? mid : r0, hi = in_a ? end : mid;
+                const uint32_t p0 = lo;
+                while (lo < hi) {
+                    const uint32_t md = (lo + hi) >> 1;
+                    if (src[md] < v) lo = md + 1; else hi = md;
                 }
-                if (hit) perm[off + written + before + __popc(bal & ((1u << lane) - 1u))] = p;
-                written += total;
-                __syncthreads();
+                dst[r0 + (i - (in_a ? r0 : mid)) + (lo - p0)] = v;
             }
+            __syncthreads();
+            uint32_t *t = src; src = dst; dst = t;
+        }
+        if (src != perm + off) {
+            for (uint32_t i = tid; i < c; i += blockDim.x) perm[off + i] = src[i];
+            __syncthreads();
         }
     }
 }
@@ -155,7 +168,7 @@ void launch_block_sort(const DevParams &P, const float *x, uint32_t n, const Sor
     k_scan_counts<<<1, 1024, 0, st>>>(s.counts, m, s.offsets, s.cursor);
     if (n == 0) return;
     k_scatter_ids<<<grid, 256, 0, st>>>(s.keys, n, s.cursor, s.perm);
-    k_segment_sort<<<grid, 256, 0, st>>>(s.offsets, s.keys, n, m, s.perm);
+    k_segment_sort<<<grid, 256, 0, st>>>(s.offsets, m, s.perm, s.keys);
 }
 
 // --------------------------------------------------------- placement

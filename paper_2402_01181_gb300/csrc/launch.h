@@ -65,9 +65,10 @@ struct SortScratch {
     uint32_t *cursor;   // nblocks
     uint32_t *perm;     // n: slot -> particle index
 };
-// keys/counts/offsets/perm of the stable counting sort of particles by the
-// block of floor(x/dx - 0.5) (x: n x 3 row-major, device).  counts must be
-// zero on entry.
+// counts/offsets/perm of the stable counting sort of particles by the block
+// of floor(x/dx - 0.5) (x: n x 3 row-major, device).  counts must be zero on
+// entry.  keys holds the per-particle keys during the sort and is left as
+// scratch (overwritten where a block holds more than 2,048 particles).
 void launch_block_sort(const DevParams &P, const float *x, uint32_t n, const SortScratch &s, Ctrl *ctrl, int grid,
                        cudaStream_t st);
 // Place particle perm[j] in slot j and build the run tables of sub-step

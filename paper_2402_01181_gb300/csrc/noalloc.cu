@@ -7,8 +7,6 @@
 // library is loaded.
 #include <cuda_runtime.h>
 
-#include <cstdio>
-#include <mutex>
 #include <string>
 
 #include "../../include/mpm.h"
@@ -21,45 +19,45 @@ namespace {
 
 // Largest grid this entry point accepts: n_grid <= 256, i.e. 64^3 blocks.
 constexpr uint32_t kMaxBlocks = 64u * 64u * 64u;
-// Layout (32-bit words): Ctrl (16 words), counts[kMaxBlocks], cursor[kMaxBlocks],
-// offsets[kMaxBlocks + 1], padding.  About 3 MB per device.
+// Layout (32-bit words): Ctrl (224 words: seven 128-byte lines),
+// counts[kMaxBlocks], cursor[kMaxBlocks], offsets[kMaxBlocks + 1], padding.
+// About 3 MB per device.
 constexpr size_t kCtrlWords = sizeof(Ctrl) / 4;
+static_assert(kCtrlWords == 224, "Ctrl is seven 128-byte lines");
 constexpr size_t kScratchWords = kCtrlWords + 3 * (size_t)kMaxBlocks + 64;
 
 static __device__ __align__(256) uint32_t g_sort_scratch[kScratchWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-uint32_t *g_scratch_addr[kMaxDevices] = {};
 mpm_status fail(mpm_status st, const std::string &msg) {
     set_last_error(msg.c_str());   // reported by mpm_last_error()
     return st;
 }
 
-// Device address of the scratch array on the current device.  Host code only
+// Device address of the scratch array in the current context.  Host code only
 // sees a host-side stand-in for g_sort_scratch, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress with the device current.  It is looked up on every
+// call, not cached: a host that drives the GPU through its own (non-primary)
+// context, or that resets the device and so gets a fresh copy of the
+// library's device code, has the array at a different address.  The first
+// lookup in a context also loads the library's device code there.
 mpm_status scratch_address(uint32_t **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(MPM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return fail(MPM_ERR_ARG, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_sort_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(MPM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch_addr[dev] = static_cast<uint32_t *>(p);
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(MPM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = static_cast<uint32_t *>(p);
     return MPM_OK;
 }
 
-// keys[j] = block of sorted entry j, from the block offsets of the sort
+// keys[j] = block of sorted entry j, from the block offsets of the sort: one
+// warp per block, its lanes writing consecutive entries of the block's segment
 __global__ void k_fill_sorted_keys(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t *__restrict__ keys) {
-    for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < m; b += gridDim.x * blockDim.x)
-        for (uint32_t j = offsets[b]; j < offsets[b + 1]; ++j) keys[j] = b;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < m; b += warps) {
+        const uint32_t first = offsets[b], last = offsets[b + 1];
+        for (uint32_t j = first + lane; j < last; j += 32u) keys[j] = b;
+    }
 }
 
 }  // namespace
@@ -100,8 +98,8 @@ extern "C" mpm_status mpm_block_sort_noalloc(const float *x, int64_t n, int32_t 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     launch_block_sort(P, x, (uint32_t)n, s, ctrl, (sms > 0 ? sms : 1) * 8, stream);
-    // the sort leaves keys in particle order; the output lists them in sorted order
-    k_fill_sorted_keys<<<(sms > 0 ? sms : 1) * 4, 256, 0, stream>>>(s.offsets, m, keys);
+    // the sort leaves keys as scratch; the output lists each sorted entry's key
+    k_fill_sorted_keys<<<(sms > 0 ? sms : 1) * 8, 256, 0, stream>>>(s.offsets, m, keys);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(MPM_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
     e = cudaStreamSynchronize(stream);
