@@ -388,10 +388,120 @@ def _frame_vector(fr) -> np.ndarray:
     return np.array(list(fr.R) + list(fr.T) + list(fr.u) + list(fr.w))
 
 
-def frame_jacobian(shape, pose0, pose1, dt, field=None, h=1e-6):
-    """d(frame entries: R, T, u, w) / d(pose0, pose1) of a one-sub-step call
-    (18 x 12), by central differences of orc_tool_frames -- the map is
-    smooth (Rodrigues and its inverse away from a half turn)."""
+def _hat(r):
+    """[r]x: the cross-product matrix of a 3-vector."""
+    return np.array([[0.0, -r[2], r[1]], [r[2], 0.0, -r[0]], [-r[1], r[0], 0.0]])
+
+
+def rotvec_to_matrix_derivative(r):
+    """dR/dr_i (i = 0, 1, 2; each 3 x 3) of Rodrigues' formula as the oracle
+    evaluates it, R = I + a K + b K^2 with K = [r]x, theta = |r|,
+    a = sin(theta)/theta and b = (1 - cos(theta))/theta^2, differentiated
+    term by term:
+        dR/dr_i = (a'/theta) r_i K + a E_i + (b'/theta) r_i K^2 + b (E_i K + K E_i),
+    E_i = [e_i]x, a'/theta = (theta cos(theta) - sin(theta))/theta^3,
+    b'/theta = (theta sin(theta) - 2 (1 - cos(theta)))/theta^4 (their Taylor
+    series below theta = 1e-3, where the closed forms cancel)."""
+    r = _f64(r, (3,))
+    th = float(np.sqrt(r @ r))
+    if th < 1e-3:
+        t2 = th * th
+        a = 1.0 - t2 / 6.0 + t2 * t2 / 120.0
+        b = 0.5 - t2 / 24.0 + t2 * t2 / 720.0
+        da = -1.0 / 3.0 + t2 / 30.0 - t2 * t2 / 840.0
+        db = -1.0 / 12.0 + t2 / 180.0 - t2 * t2 / 6720.0
+    else:
+        s, c = np.sin(th), np.cos(th)
+        a = s / th
+        b = (1.0 - c) / (th * th)
+        da = (th * c - s) / th ** 3
+        db = (th * s - 2.0 * (1.0 - c)) / th ** 4
+    K = _hat(r)
+    K2 = K @ K
+    out = np.zeros((3, 3, 3))
+    for i in range(3):
+        Ei = _hat(np.eye(3)[i])
+        out[i] = da * r[i] * K + a * Ei + db * r[i] * K2 + b * (Ei @ K + K @ Ei)
+    return out
+
+
+def matrix_to_rotvec_derivative(M):
+    """dr/dM (3 x 3 x 3: [component, row, column]) of the oracle's inverse of
+    Rodrigues' formula, r = f(theta) s with s = (M21 - M12, M02 - M20,
+    M10 - M01), theta = acos((tr M - 1)/2) and f = theta/(2 sin(theta)):
+        dr = f'(theta) (dtheta/d tr) s d(tr M) + f ds,
+    dtheta/d tr = -1/(2 sin(theta)), f' = (sin(theta) - theta cos(theta))/(2 sin(theta)^2);
+    their product g = -(sin(theta) - theta cos(theta))/(4 sin(theta)^3) is
+    taken from its Taylor series -1/12 - theta^2/30 below theta = 1e-3.
+    Rotations by close to a half turn (another branch of the inverse) are
+    not needed by the one-sub-step frames and are refused."""
+    M = _f64(M, (3, 3))
+    c = min(1.0, max(-1.0, 0.5 * (np.trace(M) - 1.0)))
+    th = float(np.arccos(c))
+    if th > np.pi - 1e-6:
+        raise ValueError("matrix_to_rotvec_derivative: rotation too close to a half turn")
+    sv = np.array([M[2, 1] - M[1, 2], M[0, 2] - M[2, 0], M[1, 0] - M[0, 1]])
+    if th < 1e-3:
+        t2 = th * th
+        f = 0.5 + t2 / 12.0 + 7.0 * t2 * t2 / 720.0
+        g = -1.0 / 12.0 - t2 / 30.0
+    else:
+        sn = np.sin(th)
+        f = th / (2.0 * sn)
+        g = -(sn - th * np.cos(th)) / (4.0 * sn ** 3)
+    ds = np.zeros((3, 3, 3))          # ds_a / dM_jk
+    for a, (j, k) in enumerate(((2, 1), (0, 2), (1, 0))):
+        ds[a, j, k] = 1.0
+        ds[a, k, j] = -1.0
+    out = f * ds
+    for a in range(3):
+        out[a] += g * sv[a] * np.eye(3)
+    return out
+
+
+def frame_jacobian(shape, pose0, pose1, dt, field=None):
+    """d(frame entries: R row-major, T, u, w) / d(pose0, pose1) of a
+    one-sub-step call (18 x 12), in closed form.  The frame map (reading
+    r12 of Eq. 11's tool pose stream, as orc_tool_frames computes it) at the
+    fraction s = 1 of a call of span dt is
+        M = R(r1) R(r0)^T,  phi = log M,  R = exp(s phi) R(r0),
+        T = T0 + s (T1 - T0),  u = (T1 - T0)/span,  w = phi/span,
+    and its derivative is taken by the chain rule through
+    rotvec_to_matrix_derivative (exp) and matrix_to_rotvec_derivative
+    (log).  shape and field do not enter the frame."""
+    p0, p1 = _f64(pose0, (6,)), _f64(pose1, (6,))
+    s, span = 1.0, float(dt)
+    R0, R1 = rotvec_to_matrix(p0[3:]), rotvec_to_matrix(p1[3:])
+    dR0, dR1 = rotvec_to_matrix_derivative(p0[3:]), rotvec_to_matrix_derivative(p1[3:])
+    M = R1 @ R0.T
+    phi = matrix_to_rotvec(M)
+    dlog = matrix_to_rotvec_derivative(M)
+    # dphi/dr0_i and dphi/dr1_i
+    dphi0 = np.stack([np.einsum("ajk,jk->a", dlog, R1 @ dR0[i].T) for i in range(3)], axis=1)
+    dphi1 = np.stack([np.einsum("ajk,jk->a", dlog, dR1[i] @ R0.T) for i in range(3)], axis=1)
+    Es = rotvec_to_matrix(s * phi)
+    dEs = rotvec_to_matrix_derivative(s * phi)
+    J = np.zeros((18, 12))
+    for i in range(3):
+        # R = exp(s phi) R0
+        dE0 = sum(dEs[a] * s * dphi0[a, i] for a in range(3))
+        dE1 = sum(dEs[a] * s * dphi1[a, i] for a in range(3))
+        J[0:9, 3 + i] = (dE0 @ R0 + Es @ dR0[i]).reshape(9)
+        J[0:9, 9 + i] = (dE1 @ R0).reshape(9)
+        # T, u
+        J[9 + i, i] = 1.0 - s
+        J[9 + i, 6 + i] = s
+        J[12 + i, i] = -1.0 / span
+        J[12 + i, 6 + i] = 1.0 / span
+    # w = phi / span
+    J[15:18, 3:6] = dphi0 / span
+    J[15:18, 9:12] = dphi1 / span
+    return J
+
+
+def frame_jacobian_differences(shape, pose0, pose1, dt, field=None, h=1e-6):
+    """The same 18 x 12 matrix by central differences of orc_tool_frames
+    (an independent check of frame_jacobian, used by the pins)."""
     p = np.concatenate([_f64(pose0, (6,)), _f64(pose1, (6,))])
     J = np.zeros((18, 12))
     for c in range(12):

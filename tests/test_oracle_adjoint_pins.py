@@ -145,6 +145,60 @@ def test_rollout_gradients_match_central_differences():
         assert abs(fd - an) <= 1e-4 * max(abs(fd), 1e-6 * np.abs(g["poses"]).max()), ((k, t, c), fd, an)
 
 
+def _left_jacobian(r):
+    """The left Jacobian of SO(3) in its textbook closed form,
+    J(r) = I + (1 - cos t)/t^2 [r]x + (t - sin t)/t^3 [r]x^2, t = |r|: the
+    derivative of the rotation vector of R(r + e) R(r)^T at e = 0."""
+    t = float(np.linalg.norm(r))
+    K = np.array([[0.0, -r[2], r[1]], [r[2], 0.0, -r[0]], [-r[1], r[0], 0.0]])
+    return np.eye(3) + (1 - np.cos(t)) / t ** 2 * K + (t - np.sin(t)) / t ** 3 * K @ K
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_frame_jacobian_matches_central_differences(case):
+    """The closed-form derivative of the one-sub-step frame map (Rodrigues'
+    formula and its inverse) against central differences of the oracle's
+    forward frames (orc_tool_frames), from rotations below the series
+    threshold of the closed forms to rotations of ~1 rad and relative turns
+    of up to 0.4 rad within the call."""
+    rng = np.random.default_rng(40 + case)
+    rot = (1e-5, 5e-4, 0.3, 1.2, 2.5, 0.05)[case]
+    turn = (1e-6, 2e-4, 0.02, 0.4, 0.1, 0.3)[case]
+    p0 = np.concatenate([rng.uniform(0.3, 0.7, 3), rot * rng.normal(size=3) / np.sqrt(3)])
+    p1 = p0 + np.concatenate([1e-3 * rng.normal(size=3), turn * rng.normal(size=3) / np.sqrt(3)])
+    dt = 5e-5
+    shape = scenes.capsule_shape(0.02, 0.15)
+    Ja = O.frame_jacobian(shape, p0, p1, dt)
+    Jd = O.frame_jacobian_differences(shape, p0, p1, dt, h=1e-5)
+    for row in range(18):
+        scale = max(np.abs(Jd[row]).max(), 1e-12)
+        assert np.abs(Ja[row] - Jd[row]).max() <= 1e-6 * scale, (row, Ja[row], Jd[row])
+
+
+def test_frame_jacobian_closed_forms():
+    """Special cases the derivative must reproduce exactly: with one sub-step
+    per call the frame's R is R(r1) and T is T1, so neither depends on pose0;
+    u = (T1 - T0)/dt; at r0 = r1 = r the angular velocity w = log(R1 R0^T)/dt
+    moves by J(r)/dt with r1 and by -J(r)/dt with r0 (J: the left Jacobian
+    of SO(3)); at r = 0, dR/dr_i is the generator [e_i]x."""
+    dt = 1e-4
+    shape = scenes.capsule_shape(0.02, 0.15)
+    for r in (np.zeros(3), np.array([0.3, -0.5, 0.8]), np.array([1e-4, 2e-4, -1e-4])):
+        p = np.concatenate([[0.4, 0.5, 0.6], r])
+        J = O.frame_jacobian(shape, p, p, dt)
+        assert np.abs(J[0:12, 0:6]).max() <= 1e-12                       # R, T independent of pose0
+        assert np.allclose(J[9:12, 6:9], np.eye(3), atol=0) and np.abs(J[9:12, 9:12]).max() == 0
+        assert np.allclose(J[12:15, 0:3], -np.eye(3) / dt, rtol=1e-15) and np.allclose(J[12:15, 6:9], np.eye(3) / dt)
+        Jl = np.eye(3) if not r.any() else _left_jacobian(r)
+        assert np.abs(J[15:18, 9:12] - Jl / dt).max() <= 1e-9 / dt
+        assert np.abs(J[15:18, 3:6] + Jl / dt).max() <= 1e-9 / dt
+    J = O.frame_jacobian(shape, np.zeros(6), np.zeros(6), dt)
+    for i in range(3):
+        gen = np.zeros((3, 3))
+        gen[(i + 2) % 3, (i + 1) % 3], gen[(i + 1) % 3, (i + 2) % 3] = 1.0, -1.0
+        assert np.array_equal(J[0:9, 9 + i].reshape(3, 3), gen)
+
+
 @pytest.mark.parametrize("block", ["x", "v"])
 def test_step_adjoint_near_the_walls_matches_central_differences(block):
     """Particles resting near the floor and a side wall, whose stencils reach

@@ -1,7 +1,10 @@
 """The oracle's pins have teeth: plant a plausible mistake in a copy of the
 oracle source (a dropped term, a wrong sign, a transposed operand, a wrong
 index, the garbled printed form of Eq. 5; in the forward step and in its
-adjoint), build it, and check that the pin suites fail on it.  Runs on the CPU only; the real oracle is untouched."""
+adjoint), build it, and check that the pin suites fail on it.  The same for
+the Python part of the oracle (the closed-form derivative of the tool frame
+map used by the rollout gradients), loaded in place of oracle/oracle.py in a
+child process.  Runs on the CPU only; the real oracle is untouched."""
 import os
 import subprocess
 import sys
@@ -120,4 +123,46 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", _suite(name))],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "planted mistake '%s' passed every pin" % name
+
+
+PY_SRC = os.path.join(ROOT, "oracle", "oracle.py")
+
+PY_MUTATIONS = {
+    "adjoint frame: Rodrigues slope term dropped": ("out[i] = da * r[i] * K + a * Ei + db * r[i] * K2",
+                                                    "out[i] = a * Ei + db * r[i] * K2"),
+    "adjoint frame: R0 derivative not transposed": ("np.einsum(\"ajk,jk->a\", dlog, R1 @ dR0[i].T)",
+                                                    "np.einsum(\"ajk,jk->a\", dlog, R1 @ dR0[i])"),
+    "adjoint frame: log trace term dropped": ("out[a] += g * sv[a] * np.eye(3)", "out[a] += 0.0 * sv[a] * np.eye(3)"),
+    "adjoint frame: linear velocity sign": ("J[12 + i, i] = -1.0 / span", "J[12 + i, i] = 1.0 / span"),
+    "adjoint frame: exp(s phi) R0 drops the R0 derivative": ("J[0:9, 3 + i] = (dE0 @ R0 + Es @ dR0[i]).reshape(9)",
+                                                              "J[0:9, 3 + i] = (dE0 @ R0).reshape(9)"),
+}
+
+_DRIVER = """
+import importlib.util, sys
+sys.path.insert(0, %r)
+import oracle as pkg
+spec = importlib.util.spec_from_file_location("oracle.oracle", %r)
+mod = importlib.util.module_from_spec(spec)
+sys.modules["oracle.oracle"] = mod
+spec.loader.exec_module(mod)
+pkg.oracle = mod
+import pytest
+sys.exit(pytest.main(["-q", "-x", "-p", "no:cacheprovider", %r]))
+"""
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_pins_catch_planted_python_mistake(name, tmp_path):
+    from oracle import oracle as O
+    old, new = PY_MUTATIONS[name]
+    src = open(PY_SRC).read()
+    assert src.count(old) == 1, "mutation anchor must be unique: " + name
+    mutated = tmp_path / "oracle.py"
+    mutated.write_text(src.replace(old, new))
+    env = dict(os.environ, ORACLE_LIB=O.build())
+    code = _DRIVER % (ROOT, str(mutated), os.path.join(ROOT, "tests", _suite(name)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr
     assert r.returncode != 0, "planted mistake '%s' passed every pin" % name
