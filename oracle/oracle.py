@@ -529,6 +529,48 @@ def rollout_frames(tools, pose_init, poses, dt):
     return out, nt
 
 
+def _frames_getter(frames, nt):
+    fsz = ct.sizeof(ToolFrame)
+
+    def frames_at(k):
+        arr = (ToolFrame * max(1, nt))()
+        if nt:
+            ct.memmove(arr, ct.byref(frames, k * nt * fsz), nt * fsz)
+        return arr
+    return frames_at
+
+
+def _reverse_segment(prm, seg, k0, frames_at, nt, bar, lame, fbar):
+    """Reverse mode of the sub-steps k0 .. k0+len(seg)-1 whose input states
+    are seg[j]: the adjoint of the state after the last of them (bar) is
+    carried back to the state before the first; lame and fbar accumulate
+    the material and frame adjoints."""
+    for j in range(len(seg) - 1, -1, -1):
+        k = k0 + j
+        bar, lb, tb = step_adjoint(prm, seg[j], frames_at(k), nt, bar)
+        lame += lb
+        if nt:
+            fbar[k] = tb
+    return bar
+
+
+def _gradients(prm, tools, pose_init, poses, lame, fbar):
+    """dL/dE, dL/dnu from the Lame adjoints (Eq. 6) and dL/dposes from the
+    frame adjoints through the frame map (each sub-step's frame depends on
+    the pose before it and its own pose)."""
+    Eb, nub = lame_vjp(prm.E, prm.nu, lame[0], lame[1])
+    pose_bar = np.zeros_like(poses)
+    for k in range(poses.shape[0]):
+        for t, tool in enumerate(tools):
+            p0 = pose_init[t] if k == 0 else poses[k - 1, t]
+            J = frame_jacobian(tool.shape, p0, poses[k, t], prm.dt, getattr(tool, "field", None))
+            g = J.T @ fbar[k, t]
+            pose_bar[k, t] += g[6:]
+            if k > 0:
+                pose_bar[k - 1, t] += g[:6]
+    return Eb, nub, pose_bar
+
+
 def rollout_loss_and_gradients(prm: OracleParams, st0: State, tools, pose_init, poses, target,
                                checkpoint=50, final_bar=None):
     """A rollout of K = len(poses) sub-steps from st0 (unchanged) and the
@@ -539,14 +581,7 @@ def rollout_loss_and_gradients(prm: OracleParams, st0: State, tools, pose_init, 
     poses = np.asarray(poses, dtype=np.float64)
     K = poses.shape[0]
     frames, nt = rollout_frames(tools, pose_init, poses, prm.dt)
-    fsz = ct.sizeof(ToolFrame)
-
-    def frames_at(k):
-        arr = (ToolFrame * max(1, nt))()
-        if nt:
-            ct.memmove(arr, ct.byref(frames, k * nt * fsz), nt * fsz)
-        return arr
-
+    frames_at = _frames_getter(frames, nt)
     cps = {}
     st = st0.copy()
     for k in range(K):
@@ -568,24 +603,31 @@ def rollout_loss_and_gradients(prm: OracleParams, st0: State, tools, pose_init, 
             s = seg[-1].copy()
             run(prm, s, 1, frames_at(k), nt)
             seg.append(s)
-        for j in range(len(seg) - 1, -1, -1):
-            k = c0 + j
-            bar, lb, tb = step_adjoint(prm, seg[j], frames_at(k), nt, bar)
-            lame += lb
-            if nt:
-                fbar[k] = tb
-    Eb, nub = lame_vjp(prm.E, prm.nu, lame[0], lame[1])
-    pose_bar = np.zeros_like(poses)
-    for k in range(K):
-        for t, tool in enumerate(tools):
-            p0 = pose_init[t] if k == 0 else poses[k - 1, t]
-            J = frame_jacobian(tool.shape, p0, poses[k, t], prm.dt, getattr(tool, "field", None))
-            g = J.T @ fbar[k, t]
-            pose_bar[k, t] += g[6:]
-            if k > 0:
-                pose_bar[k - 1, t] += g[:6]
+        bar = _reverse_segment(prm, seg, c0, frames_at, nt, bar, lame, fbar)
+    Eb, nub, pose_bar = _gradients(prm, tools, pose_init, poses, lame, fbar)
     return {"loss": loss, "E": Eb, "nu": nub, "poses": pose_bar, "state0": bar, "final": final,
             "lame": lame, "frames": fbar}
+
+
+def reverse_from_states(prm: OracleParams, states, tools, pose_init, poses, bar):
+    """Reverse mode of K = len(poses) sub-steps along a given forward
+    trajectory: states[k] is the state before sub-step k (k = 0 .. K-1),
+    bar the adjoint of the state after the last sub-step.  Each sub-step's
+    adjoint is evaluated at its given input state (its forward pass is
+    recomputed from that state alone), so a trajectory computed elsewhere --
+    in another precision -- enters only through the states it supplies.
+    Returns the gradients with respect to E, nu, the poses and states[0]."""
+    poses = np.asarray(poses, dtype=np.float64)
+    K = poses.shape[0]
+    assert len(states) == K
+    frames, nt = rollout_frames(tools, pose_init, poses, prm.dt)
+    frames_at = _frames_getter(frames, nt)
+    bar = {k: _f64(v).copy() for k, v in bar.items()}
+    lame = np.zeros(2)
+    fbar = np.zeros((K, nt, 18))
+    bar = _reverse_segment(prm, list(states), 0, frames_at, nt, bar, lame, fbar)
+    Eb, nub, pose_bar = _gradients(prm, tools, pose_init, poses, lame, fbar)
+    return {"E": Eb, "nu": nub, "poses": pose_bar, "state0": bar, "lame": lame, "frames": fbar}
 
 
 # ----------------------------------------------------------- the surface

@@ -236,3 +236,81 @@ def test_config5_full_size_gradients_match_oracle(M):
     assert abs(nu.grad.item() - ref["nu"]) <= 3e-2 * abs(ref["nu"]), (nu.grad.item(), ref["nu"])
     gp = P.grad.numpy()
     assert np.abs(gp - ref["poses"]).max() <= 5e-2 * np.abs(ref["poses"]).max()
+
+
+def _segment_errors(got, ref):
+    """Relative errors of one segment's gradients: E and nu against their own
+    magnitude; each pose component (tool, coordinate) against its largest
+    magnitude over the segment; each block of the incoming state adjoint
+    against its largest magnitude."""
+    out = {"E": abs(got["E"] - ref["E"]) / abs(ref["E"]), "nu": abs(got["nu"] - ref["nu"]) / abs(ref["nu"])}
+    scale = np.abs(ref["poses"]).max(axis=0, keepdims=True)
+    out["poses"] = float((np.abs(got["poses"] - ref["poses"]) / np.maximum(scale, 1e-300)).max())
+    for k in ("x", "v", "F", "C"):
+        r = ref["state0"][k]
+        out[k] = float(np.abs(got[k] - r).max() / np.abs(r).max())
+    return out
+
+
+def test_config5_segments_match_oracle_adjoint(M):
+    """The benchmark's differentiable workload (the 30K slab, 500 sub-steps,
+    checkpoints every 50) reversed one 50-sub-step segment at a time, on the
+    GPU (mpm_tape_record / mpm_tape_backward from the GPU's own checkpoint
+    state) and in the FP64 oracle, both seeded with the same incoming adjoint
+    (the GPU's, from the segment after it; the loss gradient for the last).
+    The oracle reverses each sub-step at the GPU's own forward state of that
+    sub-step, so no FP32 drift of the forward trajectory enters: what is
+    compared is the adjoint's arithmetic.  Per segment, dL/dE, dL/dnu, every
+    pose entry (against the largest entry of its coordinate in the segment)
+    and the outgoing state adjoint agree to 1e-3."""
+    import torch
+    case = scenes.slab30k_diff()
+    sc = case.scene
+    prm = O.OracleParams.from_scene(sc)
+    K, ck = case.poses.shape[0], case.checkpoint
+    tool = sc.tools[0]
+    dev = torch.device("cuda")
+
+    def seg_sim(state, pose_start):
+        sim = M.sim_from_scene(sc, pipeline=M.MPM_PIPELINE_SPLIT, load=False)
+        sim.load(state["x"], sc.particle_volume, state["v"], state["F"], state["C"])
+        sim.set_tool(0, pose_start, tool.shape)
+        return sim
+
+    # the GPU's forward trajectory, one sub-step per recorded call
+    sim = M.sim_from_scene(sc, pipeline=M.MPM_PIPELINE_SPLIT, load=False)
+    sim.load(sc.x, sc.particle_volume)
+    sim.set_tool(0, case.pose_init[0], tool.shape)
+    states = []
+    for k in range(K):
+        states.append(sim.read())
+        sim.tape_record(case.poses[k:k + 1], 1)
+    final = sim.read()
+    sim.close()
+    starts = [case.pose_init[0]] + [case.poses[s * ck - 1, 0] for s in range(1, K // ck)]
+    # the loss seed from the FP64 target rollout
+    tprm = O.OracleParams(**{**prm.__dict__, "E": case.target_E, "nu": case.target_nu})
+    tgt = O.State(sc.x)
+    tf, nt = O.rollout_frames(sc.tools, case.pose_init, case.target_poses, prm.dt)
+    O.run(tprm, tgt, K, tf, nt)
+    seed = {"x": (2.0 * (final["x"].astype(np.float64) - tgt.x) / sc.n).astype(np.float32),
+            "v": np.zeros((sc.n, 3), np.float32), "F": np.zeros((sc.n, 9), np.float32),
+            "C": np.zeros((sc.n, 9), np.float32)}
+    worst = {}
+    for s in range(K // ck - 1, -1, -1):
+        seg_poses = case.poses[s * ck:(s + 1) * ck]
+        sim = seg_sim(states[s * ck], starts[s])
+        sim.tape_record(seg_poses, ck)
+        g = sim.tape_backward(*[torch.tensor(seed[k], device=dev) for k in ("x", "v", "F", "C")], want_state=True)
+        sim.close()
+        got = {"E": g["E"], "nu": g["nu"], "poses": g["poses"]}
+        got.update({k: g[k].cpu().numpy().astype(np.float64) for k in ("x", "v", "F", "C")})
+        seg_states = [O.State(st["x"], st["v"], st["C"], st["F"]) for st in states[s * ck:(s + 1) * ck]]
+        ref = O.reverse_from_states(prm, seg_states, sc.tools, starts[s][None], seg_poses,
+                                    {k: seed[k].astype(np.float64) for k in ("x", "v", "F", "C")})
+        err = _segment_errors(got, ref)
+        for k, v in err.items():
+            worst[k] = max(worst.get(k, 0.0), v)
+        assert all(v <= 1e-3 for v in err.values()), (s, err)
+        seed = {k: g[k].cpu().numpy() for k in ("x", "v", "F", "C")}    # the GPU's own adjoint, upstream
+    print("config-5 per-segment worst relative errors:", worst)

@@ -226,3 +226,27 @@ def test_step_adjoint_near_the_walls_matches_central_differences(block):
         fd = (_dot(ybar, _step(prm, a, frames, 0)) - _dot(ybar, _step(prm, b, frames, 0))) / (2 * h)
         an = float(np.sum(xbar[block] * d))
         assert abs(fd - an) <= 1e-5 * abs(fd), (block, trial, fd, an)
+
+
+def test_reverse_from_states_is_the_rollout_reverse():
+    """Given the oracle's own forward states, the reverse along a supplied
+    trajectory is the checkpointed rollout's reverse: the same sub-step
+    adjoints in the same order, so the results are identical."""
+    prm, st, tools, p0, p1 = _scene(seed=5, dt=2e-3)
+    K = 4
+    poses = np.stack([p0 + (k + 1) * (p1 - p0) for k in range(K)])
+    target = st.x + 0.01
+    ref = O.rollout_loss_and_gradients(prm, st, tools, p0, poses, target, checkpoint=3)
+    frames, nt = O.rollout_frames(tools, p0, poses, prm.dt)
+    states, s = [], st.copy()
+    for k in range(K):
+        states.append(s.copy())
+        arr = (O.ToolFrame * nt)()
+        for t in range(nt):
+            arr[t] = frames[k * nt + t]
+        O.run(prm, s, 1, arr, nt)
+    got = O.reverse_from_states(prm, states, tools, p0, poses, {"x": 2.0 * (s.x - target) / s.n})
+    assert got["E"] == ref["E"] and got["nu"] == ref["nu"]
+    assert np.array_equal(got["poses"], ref["poses"])
+    for k in ("x", "v", "C", "F"):
+        assert np.array_equal(got["state0"][k], ref["state0"][k])
