@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-environment measurement")
     ap.add_argument("--batch-envs", type=int, default=256)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the 8M block and the split-pipeline sub-lines")
     return ap.parse_args()
 
 
@@ -424,9 +425,11 @@ def run_differentiable(args, rank, device, barrier, max_over_ranks, reps=2):
     """The differentiable rollout: the 30K slab over 500
     sub-steps with checkpoints every 50, loss = mean |x(T) - target|^2 with
     a target rolled out on the GPU with E = 1.2e4, nu = 0.33 and shifted
-    poses.  Times the recorded forward pass (mpm_tape_record) and the reverse
-    pass (mpm_tape_backward, which recomputes every segment), against a
-    plain split-pipeline forward of the same sub-steps."""
+    poses.  On the fused pipeline (the product path) and, for comparison, on
+    the unsorted split pipeline: the recorded forward pass (mpm_tape_record)
+    and the reverse pass (mpm_tape_backward, which recomputes every segment),
+    against the plain fused forward of the same 500 sub-steps (20 calls of
+    25 sub-steps, as the benchmark steps the slab)."""
     import torch
     from paper_2402_01181_gb300 import dist as D
     from paper_2402_01181_gb300 import mpm
@@ -435,59 +438,68 @@ def run_differentiable(args, rank, device, barrier, max_over_ranks, reps=2):
     K = case.poses.shape[0]
     stream = torch.cuda.current_stream(device)
 
-    def fresh(E, nu, poses, record=True):
-        si = mpm.sim_from_scene(sc, pipeline=mpm.MPM_PIPELINE_SPLIT, load=False)
+    def fresh(E, nu, pipe):
+        si = mpm.sim_from_scene(sc, pipeline=pipe, load=False)
         si.set_env_material(0, E, nu, sc.rho)
         si.load(sc.x, sc.particle_volume)
         si.set_tool(0, case.pose_init[0], sc.tools[0].shape)
         return si
 
-    tgt = fresh(case.target_E, case.target_nu, case.target_poses)
+    tgt = fresh(case.target_E, case.target_nu, mpm.MPM_PIPELINE_FUSED)
     tgt.tape_record(case.target_poses, case.checkpoint)
     target = torch.tensor(tgt.read()["x"], device=device)
     tgt.close()
-    fwd, bwd, plain = [], [], []
-    res = {}
+
+    def timed(pipe):
+        fwd, bwd, res = [], [], {}
+        for r in range(reps + 1):
+            si = fresh(sc.E, sc.nu, pipe)
+            a, b, c0, c = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+            barrier()
+            a.record(stream)
+            si.tape_record(case.poses, case.checkpoint)
+            b.record(stream)
+            x = torch.empty((sc.n, 3), dtype=torch.float32, device=device)
+            si.read_device(x=x)
+            loss = float(((x - target) ** 2).sum(dim=1).mean())
+            gx = 2.0 * (x - target) / sc.n
+            torch.cuda.synchronize(device)
+            c0.record(stream)
+            g = si.tape_backward(gx)
+            c.record(stream)
+            torch.cuda.synchronize(device)
+            si.close()
+            if r == 0:
+                continue                      # warm-up
+            fwd.append(a.elapsed_time(b))
+            bwd.append(c0.elapsed_time(c))
+            res = {"loss": loss, "dL_dE": g["E"], "dL_dnu": g["nu"], "max_abs_dL_dpose": float(abs(g["poses"]).max())}
+        return max_over_ranks(min(fwd)), max_over_ranks(min(bwd)), res
+
+    f, bk, res = timed(mpm.MPM_PIPELINE_FUSED)
+    fs, bks, _ = timed(mpm.MPM_PIPELINE_SPLIT)
+    # the plain fused forward of the same sub-steps: 20 calls of 25
+    plain = []
+    S = 25
     for r in range(reps + 1):
-        si = fresh(sc.E, sc.nu, case.poses)
-        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        barrier()
-        a.record(stream)
-        si.tape_record(case.poses, case.checkpoint)
-        b.record(stream)
-        x = torch.empty((sc.n, 3), dtype=torch.float32, device=device)
-        si.read_device(x=x)
-        loss = float(((x - target) ** 2).sum(dim=1).mean())
-        gx = 2.0 * (x - target) / sc.n
-        torch.cuda.synchronize(device)
-        c0 = torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        g = si.tape_backward(gx)
-        c.record(stream)
-        torch.cuda.synchronize(device)
-        si.close()
-        # the same sub-steps without the record: one mpm_step call per pose
-        sp = fresh(sc.E, sc.nu, case.poses)
+        sp = fresh(sc.E, sc.nu, mpm.MPM_PIPELINE_FUSED)
         d, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(device)
         d.record(stream)
-        for k in range(K):
-            sp.set_tool(0, case.poses[k, 0], sc.tools[0].shape)
-            sp.step(1)
+        for k0 in range(0, K, S):
+            sp.set_tool(0, case.poses[k0 + S - 1, 0], sc.tools[0].shape)
+            sp.step(S)
         e.record(stream)
         torch.cuda.synchronize(device)
         sp.close()
-        if r == 0:
-            continue                      # warm-up
-        fwd.append(a.elapsed_time(b))
-        bwd.append(c0.elapsed_time(c))
-        plain.append(d.elapsed_time(e))
-        res = {"loss": loss, "dL_dE": g["E"], "dL_dnu": g["nu"],
-               "max_abs_dL_dpose": float(abs(g["poses"]).max())}
-    f, bk, pl = max_over_ranks(min(fwd)), max_over_ranks(min(bwd)), max_over_ranks(min(plain))
+        if r > 0:
+            plain.append(d.elapsed_time(e))
+    pl = max_over_ranks(min(plain))
     res.update({"workload": "slab30k_diff", "particles": sc.n, "substeps": K, "checkpoint_every": case.checkpoint,
-                "forward_record_ms": f, "backward_ms": bk, "plain_forward_ms": pl,
-                "backward_over_forward": bk / f, "backward_over_plain_forward": bk / pl,
-                "note": "min over %d repetitions; backward includes the segment recomputation" % reps})
+                "pipeline": "fused", "forward_record_ms": f, "backward_ms": bk, "fused_forward_ms": pl,
+                "backward_over_fused_forward": bk / pl, "backward_over_recorded_forward": bk / f,
+                "split": {"forward_record_ms": fs, "backward_ms": bks, "backward_over_fused_forward": bks / pl},
+                "note": "min over %d repetitions; the backward includes the segment recomputation" % reps})
     return res
 
 
@@ -592,6 +604,32 @@ def time_oracle(name, budget_s, rank_seed=0, max_steps=50):
         done, name, sc.n, sc.n_grid)
 
 
+def time_oracle_adjoint(substeps=20, checkpoint=10):
+    """Time the FP64 oracle's forward rollout and its reverse mode on the first
+    sub-steps of the differentiable workload (the 30K slab, loss on the final
+    positions); returns particle-steps/s of each and the sample."""
+    from oracle import oracle as O
+    case = scenes.slab30k_diff(steps=substeps, checkpoint=checkpoint)
+    sc = case.scene
+    prm = O.OracleParams.from_scene(sc)
+    st0 = O.State(sc.x)
+    t0 = time.perf_counter()
+    st = st0.copy()
+    fr, nt = O.rollout_frames(sc.tools, case.pose_init, case.poses, prm.dt)
+    O.run(prm, st, substeps, fr, nt)
+    t_fwd = time.perf_counter() - t0
+    target = st.x + 1e-5
+    t0 = time.perf_counter()
+    O.rollout_loss_and_gradients(prm, st0, sc.tools, case.pose_init, case.poses, target, checkpoint=checkpoint)
+    t_all = time.perf_counter() - t0
+    units = sc.n * substeps
+    return {"forward_particle_steps_per_s": units / t_fwd,
+            "backward_particle_steps_per_s": units / max(t_all - t_fwd, 1e-9),
+            "backward_over_forward": (t_all - t_fwd) / t_fwd, "cores": 1,
+            "sample": "%d sub-steps of the differentiable workload (%d particles), checkpoints every %d; the "
+                      "backward includes the recomputation of the segments" % (substeps, sc.n, checkpoint)}
+
+
 def reference_main(args):
     from paper_2402_01181_gb300 import dist as D
     world, rank, local = D.env()
@@ -653,6 +691,27 @@ def main():
         second["sampled_field"] = {"workload": "slab30k_sdf", "field_res": 256,
                                    "value": r3["n"] * S * r3["steps"] * world / (r3["t_ms"] / 1e3),
                                    "ms_per_step": r3["t_ms"] / r3["steps"]}
+
+    # the roofline sweep of the benchmark plan: the 8M block (256^3 grid), and
+    # sorted (fused) against unsorted (split) P2G on both blocks
+    sweep = None
+    if not args.no_sweep and args.workload == "block1m" and args.pipeline == "fused":
+        sweep = {}
+        split_args = argparse.Namespace(**{**vars(args), "pipeline": "split"})
+        for wl, a, key in (("block8m", args, "block8m_fused"), ("block1m", split_args, "block1m_split"),
+                           ("block8m", split_args, "block8m_split")):
+            steps = 10 if wl == "block8m" else args.steps
+            r = run_gpu_workload(wl, a, rank, device, barrier, max_over_ranks, with_e2e=False, steps=steps)
+            n_units_w = r["n"] * S * r["steps"] * world
+            bpp_w = survey_bytes_per_particle_step(r["n"], r["active_nodes"])
+            launch_w = r["t_ms"] / (r["steps"] * S)
+            sweep[key] = {"workload": wl, "pipeline": a.pipeline, "n_particles": r["n"], "n_grid": r["n_grid"],
+                          "value": n_units_w / (r["t_ms"] / 1e3), "unit": "particle-steps/s",
+                          "us_per_substep": launch_w * 1e3, "tuning": r["tuning"], "clocks": r["clocks"],
+                          "roofline_frac": bpp_w * r["n"] / (launch_w / 1e3) / 1e9 / measured_peak()[0]}
+        for wl in ("block1m", "block8m"):
+            fused_v = value if wl == "block1m" else sweep["block8m_fused"]["value"]
+            sweep["%s_sorted_over_unsorted" % wl] = fused_v / sweep["%s_split" % wl]["value"]
 
     batched = None
     if not args.no_batched:
@@ -718,6 +777,8 @@ def main():
         v, sample = time_oracle(args.workload, 15.0)
         cpu = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample,
                **cpu_description()}
+        if differentiable is not None:
+            differentiable["oracle"] = time_oracle_adjoint()
     e2e_val = main_res["n"] * S * args.steps * world / (main_res["t_e2e_ms"] / 1e3)
     launches_per_frame = S if args.pipeline == "fused" else 3 * S
     line = {
@@ -739,6 +800,7 @@ def main():
         "gpu_launches": launches_per_frame * args.steps,
         "clocks": main_res["clocks"],
         "secondary": second,
+        "sweep": sweep,
         "batched": batched,
         "differentiable": differentiable,
         "surface": surface,

@@ -691,10 +691,16 @@ void orc_lame_vjp(double E, double nu, double mu_bar, double lam_bar, double *E_
  * accumulates dL/dmu, dL/dlam; tool_bar (ntools x 18: R row-major, T, u, w
  * of each frame) accumulates dL/d(frame entries).  Returns -1 if scratch
  * memory could not be allocated, else 0. */
-int orc_step_adjoint(const orc_params *p, const orc_tool *tools, int32_t ntools, int64_t N,
-                     const double *x, const double *v, const double *C, const double *F,
-                     double *xb, double *vb, double *Cb, double *Fb,
-                     double *lame_bar, double *tool_bar)
+/* grid_m, grid_mv: if not NULL, the grid (mass, momentum) the sub-step's
+ * grid operation reads, in place of the P2G of (x, v, C, F); the reverse of
+ * P2G still differentiates the P2G of the particles.  This evaluates the
+ * grid operation and G2P, and their derivatives, at a grid computed
+ * elsewhere (in another precision). */
+static int step_adjoint_impl(const orc_params *p, const orc_tool *tools, int32_t ntools, int64_t N,
+                             const double *x, const double *v, const double *C, const double *F,
+                             const double *grid_m, const double *grid_mv,
+                             double *xb, double *vb, double *Cb, double *Fb,
+                             double *lame_bar, double *tool_bar)
 {
     const int n = p->n_grid;
     const double dx = 1.0 / n, K = 4.0 / (dx * dx), dt = p->dt;
@@ -713,7 +719,12 @@ int orc_step_adjoint(const orc_params *p, const orc_tool *tools, int32_t ntools,
         return -1;
     }
     /* the forward pass up to the grid velocities */
-    orc_p2g(p, N, x, v, C, F, gm, gmv, NULL);
+    if (grid_m && grid_mv) {
+        memcpy(gm, grid_m, sizeof(double) * nn);
+        memcpy(gmv, grid_mv, sizeof(double) * 3 * nn);
+    } else {
+        orc_p2g(p, N, x, v, C, F, gm, gmv, NULL);
+    }
     orc_grid_update(p, tools, ntools, gm, gmv, gv, NULL, NULL);
 
     /* ---- G2P (Eqs. 4, 8-10) backwards */
@@ -929,6 +940,24 @@ int orc_step_adjoint(const orc_params *p, const orc_tool *tools, int32_t ntools,
     }
     free(gm); free(gmv); free(gv); free(gvb); free(gmb); free(gmvb);
     return 0;
+}
+
+int orc_step_adjoint(const orc_params *p, const orc_tool *tools, int32_t ntools, int64_t N,
+                     const double *x, const double *v, const double *C, const double *F,
+                     double *xb, double *vb, double *Cb, double *Fb,
+                     double *lame_bar, double *tool_bar)
+{
+    return step_adjoint_impl(p, tools, ntools, N, x, v, C, F, NULL, NULL, xb, vb, Cb, Fb, lame_bar, tool_bar);
+}
+
+int orc_step_adjoint_at_grid(const orc_params *p, const orc_tool *tools, int32_t ntools, int64_t N,
+                             const double *x, const double *v, const double *C, const double *F,
+                             const double *grid_m, const double *grid_mv,
+                             double *xb, double *vb, double *Cb, double *Fb,
+                             double *lame_bar, double *tool_bar)
+{
+    return step_adjoint_impl(p, tools, ntools, N, x, v, C, F, grid_m, grid_mv, xb, vb, Cb, Fb, lame_bar,
+                             tool_bar);
 }
 
 /* ======================================================================

@@ -96,6 +96,9 @@ def lib():
             L.orc_step_adjoint.argtypes = [P, TF, ct.c_int32, ct.c_int64, _D, _D, _D, _D, _D, _D, _D, _D,
                                            _D, _D]
             L.orc_step_adjoint.restype = ct.c_int
+            L.orc_step_adjoint_at_grid.argtypes = [P, TF, ct.c_int32, ct.c_int64, _D, _D, _D, _D, _D, _D, _D, _D,
+                                                   _D, _D, _D, _D]
+            L.orc_step_adjoint_at_grid.restype = ct.c_int
             L.orc_lame_vjp.argtypes = [ct.c_double, ct.c_double, ct.c_double, ct.c_double, _D, _D]
             L.orc_surface.argtypes = [ct.c_int32, _D, ct.c_double, ct.c_double, _D, ct.c_int64]
             L.orc_surface.restype = ct.c_int64
@@ -356,11 +359,14 @@ def sorted_order(keys: np.ndarray, previous: Optional[np.ndarray] = None) -> np.
 
 # ------------------------------------------------------------- the adjoint
 
-def step_adjoint(prm: OracleParams, st: State, frames, ntools, bar):
+def step_adjoint(prm: OracleParams, st: State, frames, ntools, bar, grid=None):
     """Reverse mode of one sub-step from state st (unchanged).  bar: dict of
     the adjoints of the state after the sub-step (x, v, C, F; missing keys are
     zero).  Returns (adjoint of the state before it, [dL/dmu, dL/dlam],
-    dL/d(frame entries) as (ntools, 18): R row-major, T, u, w)."""
+    dL/d(frame entries) as (ntools, 18): R row-major, T, u, w).  grid: an
+    (n, n, n, 4) array of (mass, momentum) to evaluate the grid operation and
+    G2P at instead of the P2G of st (a grid computed elsewhere, e.g. by the
+    GPU); the reverse of P2G still differentiates the P2G of st."""
     n = st.n
     out = {k: (np.zeros((n, c)) if bar.get(k) is None else _f64(bar[k], (n, c)).copy())
            for k, c in (("x", 3), ("v", 3), ("C", 9), ("F", 9))}
@@ -369,9 +375,18 @@ def step_adjoint(prm: OracleParams, st: State, frames, ntools, bar):
     if frames is None or ntools == 0:
         frames = (ToolFrame * 1)()
         ntools = 0
-    rc = lib().orc_step_adjoint(ct.byref(prm.c()), frames, int(ntools), n, _dp(st.x), _dp(st.v), _dp(st.C),
-                                _dp(st.F), _dp(out["x"]), _dp(out["v"]), _dp(out["C"]), _dp(out["F"]),
-                                _dp(lame), _dp(tb))
+    if grid is None:
+        rc = lib().orc_step_adjoint(ct.byref(prm.c()), frames, int(ntools), n, _dp(st.x), _dp(st.v), _dp(st.C),
+                                    _dp(st.F), _dp(out["x"]), _dp(out["v"]), _dp(out["C"]), _dp(out["F"]),
+                                    _dp(lame), _dp(tb))
+    else:
+        ng = prm.n_grid
+        g = _f64(grid, (ng ** 3, 4))
+        gm = np.ascontiguousarray(g[:, 0])
+        gmv = np.ascontiguousarray(g[:, 1:]).reshape(-1)
+        rc = lib().orc_step_adjoint_at_grid(ct.byref(prm.c()), frames, int(ntools), n, _dp(st.x), _dp(st.v),
+                                            _dp(st.C), _dp(st.F), _dp(gm), _dp(gmv), _dp(out["x"]), _dp(out["v"]),
+                                            _dp(out["C"]), _dp(out["F"]), _dp(lame), _dp(tb))
     if rc != 0:
         raise MemoryError("orc_step_adjoint: out of memory")
     return out, lame, tb[:ntools]
@@ -540,14 +555,14 @@ def _frames_getter(frames, nt):
     return frames_at
 
 
-def _reverse_segment(prm, seg, k0, frames_at, nt, bar, lame, fbar):
+def _reverse_segment(prm, seg, k0, frames_at, nt, bar, lame, fbar, grids=None):
     """Reverse mode of the sub-steps k0 .. k0+len(seg)-1 whose input states
-    are seg[j]: the adjoint of the state after the last of them (bar) is
-    carried back to the state before the first; lame and fbar accumulate
-    the material and frame adjoints."""
+    are seg[j] (and whose grids are grids[j], if given): the adjoint of the
+    state after the last of them (bar) is carried back to the state before
+    the first; lame and fbar accumulate the material and frame adjoints."""
     for j in range(len(seg) - 1, -1, -1):
         k = k0 + j
-        bar, lb, tb = step_adjoint(prm, seg[j], frames_at(k), nt, bar)
+        bar, lb, tb = step_adjoint(prm, seg[j], frames_at(k), nt, bar, None if grids is None else grids[j])
         lame += lb
         if nt:
             fbar[k] = tb
@@ -609,14 +624,16 @@ def rollout_loss_and_gradients(prm: OracleParams, st0: State, tools, pose_init, 
             "lame": lame, "frames": fbar}
 
 
-def reverse_from_states(prm: OracleParams, states, tools, pose_init, poses, bar):
+def reverse_from_states(prm: OracleParams, states, tools, pose_init, poses, bar, grids=None):
     """Reverse mode of K = len(poses) sub-steps along a given forward
     trajectory: states[k] is the state before sub-step k (k = 0 .. K-1),
     bar the adjoint of the state after the last sub-step.  Each sub-step's
     adjoint is evaluated at its given input state (its forward pass is
     recomputed from that state alone), so a trajectory computed elsewhere --
     in another precision -- enters only through the states it supplies.
-    Returns the gradients with respect to E, nu, the poses and states[0]."""
+    grids[k], if given, is the (n, n, n, 4) grid sub-step k's grid operation
+    read there (see step_adjoint).  Returns the gradients with respect to E,
+    nu, the poses and states[0]."""
     poses = np.asarray(poses, dtype=np.float64)
     K = poses.shape[0]
     assert len(states) == K
@@ -625,7 +642,7 @@ def reverse_from_states(prm: OracleParams, states, tools, pose_init, poses, bar)
     bar = {k: _f64(v).copy() for k, v in bar.items()}
     lame = np.zeros(2)
     fbar = np.zeros((K, nt, 18))
-    bar = _reverse_segment(prm, list(states), 0, frames_at, nt, bar, lame, fbar)
+    bar = _reverse_segment(prm, list(states), 0, frames_at, nt, bar, lame, fbar, grids)
     Eb, nub, pose_bar = _gradients(prm, tools, pose_init, poses, lame, fbar)
     return {"E": Eb, "nu": nub, "poses": pose_bar, "state0": bar, "lame": lame, "frames": fbar}
 

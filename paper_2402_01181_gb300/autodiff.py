@@ -1,10 +1,12 @@
 """torch.autograd binding of the differentiable rollout.
 
 `rollout(sim, E, nu, poses, x0, ...)` loads an initial particle state into a
-split-pipeline `Sim`, runs len(poses) sub-steps with the tools following the
-pose stream (mpm_tape_record) and returns the final state.  Its backward is
-mpm_tape_backward: the hand-written reverse mode of the sub-step on the GPU,
-with the particle state checkpointed every `checkpoint_every` sub-steps.
+`Sim` (either pipeline, one environment), runs len(poses) sub-steps with the
+tools following the pose stream (mpm_tape_record) and returns the final
+state.  Its backward is mpm_tape_backward: the hand-written reverse mode of
+the sub-step on the GPU (on the fused pipeline, block by block in the
+forward pass's sorted order), with the particle state checkpointed every
+`checkpoint_every` sub-steps.
 Gradients flow to E, nu (0-d tensors), poses ((K, n_tools, 6) float64) and the
 initial state (x0, v0, F0, C0).  The paper does not differentiate its
 simulator (Sec. V names it as future work); the derivative is that of the
@@ -58,6 +60,4 @@ def rollout(sim: "M.Sim", E: torch.Tensor, nu: torch.Tensor, poses: torch.Tensor
     respect to E, nu, poses and the initial state.  The tools start where
     the sim has them (place them with Sim.set_tool before the first call);
     poses[k, t] is tool t's pose at the end of sub-step k."""
-    if sim.cfg.pipeline != M.MPM_PIPELINE_SPLIT:
-        raise ValueError("rollout needs a Sim created with pipeline=MPM_PIPELINE_SPLIT")
     return _Rollout.apply(sim, float(particle_volume), int(checkpoint_every), E, nu, poses, x0, v0, F0, C0)

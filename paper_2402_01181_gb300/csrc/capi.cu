@@ -83,6 +83,24 @@ struct Tape {
     std::vector<double> pose_init;    // ntools x 6
     std::vector<double> poses;        // nsub x ntools x 6
     double E = 0, nu = 0;
+    // fused pipeline: checkpoints are particle-id-ordered images (x, v, F, C:
+    // 24 floats per particle); the segment being reversed is replayed with
+    // recording sub-steps, each keeping its input particles by block and the
+    // grid it read
+    bool fused = false;
+    float *final_img = nullptr;       // the state after the rollout (restored after the reverse pass)
+    size_t cap_final = 0, cap_rs = 0, cap_rsg = 0, cap_rsb = 0, cap_gb = 0;
+    float *rs = nullptr;              // ck x (xi, f0, f1: 12 n floats; f2: n floats padded to 4)
+    float4 *rs_grid = nullptr;        // ck x nn: the grid each recorded sub-step read
+    uint32_t *rs_blk = nullptr;       // ck x (2 nblocks block ranges + nblocks work list + 4 counters)
+    float4 *gb2 = nullptr;            // second grid adjoint buffer
+    // per grid block: a stamp, and two lists ([count, block ...]) of the blocks
+    // a reverse sub-step touches, for the current and the later sub-step
+    uint32_t *touch = nullptr;
+    size_t cap_touch = 0;
+    uint32_t touch_sv = 0;
+    double *lame_part = nullptr;      // per CTA of the reverse sub-step: dL/dmu, dL/dlambda
+    size_t cap_lame = 0;
 };
 
 }  // namespace
@@ -118,9 +136,13 @@ struct mpm_handle {
     float *staging = nullptr;   // 24 floats per particle (AoS x, v, F, C)
     float4 *dense = nullptr;    // n^3 float4, allocated on first inspection
     ToolFrame *d_frames = nullptr;
-    ToolFrame *h_frames = nullptr;   // pinned
+    // pinned frame staging, two buffers used in turn: a call waits only for the
+    // copy out of the buffer it refills (made two uploads earlier), so the host
+    // can run a call ahead of the GPU
+    ToolFrame *h_frames[2] = {nullptr, nullptr};
+    int frames_next = 0;
     uint32_t *h_err = nullptr;       // pinned copy of Ctrl::err
-    cudaEvent_t ev_err = nullptr, ev_frames = nullptr;
+    cudaEvent_t ev_err = nullptr, ev_frames[2] = {nullptr, nullptr};
     bool err_pending = false;
     std::vector<HostTool> tools;         // n_envs x MPM_MAX_TOOLS
     std::vector<HostField> fields;       // sampled distance fields, shared by every environment
@@ -132,6 +154,7 @@ struct mpm_handle {
     uint32_t *d_env_off = nullptr;
     bool envp_dirty = true;
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+    int rev_grid = 0, rec_grid = 0;   // CTAs of the reverse and recording sub-steps
     bool use_graphs = true;
     Tape tape;
     // asynchronous readback: two staging buffers (24 floats per particle), a
@@ -199,12 +222,15 @@ void release_all(mpm_handle *h) {
         }
     }
     h->allocs.clear();
-    if (h->h_frames) cudaFreeHost(h->h_frames);
+    for (int b = 0; b < 2; ++b) {
+        if (h->h_frames[b]) cudaFreeHost(h->h_frames[b]);
+        if (h->ev_frames[b]) cudaEventDestroy(h->ev_frames[b]);
+        h->h_frames[b] = nullptr;
+        h->ev_frames[b] = nullptr;
+    }
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->ev_err) cudaEventDestroy(h->ev_err);
-    if (h->ev_frames) cudaEventDestroy(h->ev_frames);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    h->h_frames = nullptr;
     h->h_err = nullptr;
 }
 
@@ -315,14 +341,16 @@ mpm_status upload_frames(mpm_handle *h, int first, int nsub, int total) {
     // tool counts can change between calls: refresh the environment table
     mpm_status st = upload_env_params(h);
     if (st != MPM_OK) return st;
-    // the pinned staging buffer may still feed an earlier copy
-    CK(cudaEventSynchronize(h->ev_frames));
+    // this staging buffer may still feed the copy of two uploads ago
+    const int fb = h->frames_next;
+    h->frames_next ^= 1;
+    CK(cudaEventSynchronize(h->ev_frames[fb]));
     if (h->tstride > 0) {
-        fill_frames(h, first, nsub, total, h->tstride, h->h_frames);
-        CK(cudaMemcpyAsync(h->d_frames, h->h_frames, sizeof(ToolFrame) * (size_t)nsub * h->n_envs * h->tstride,
+        fill_frames(h, first, nsub, total, h->tstride, h->h_frames[fb]);
+        CK(cudaMemcpyAsync(h->d_frames, h->h_frames[fb], sizeof(ToolFrame) * (size_t)nsub * h->n_envs * h->tstride,
                            cudaMemcpyHostToDevice, h->stream));
     }
-    CK(cudaEventRecord(h->ev_frames, h->stream));
+    CK(cudaEventRecord(h->ev_frames[fb], h->stream));
     return MPM_OK;
 }
 
@@ -527,16 +555,20 @@ mpm_status mpm_create(const mpm_config *cfg, void *cuda_stream, mpm_alloc_fn all
         if ((st = dalloc_t(h, &h->sort.offsets, h->nblocks + 1)) != MPM_OK) return bail(st);
         if ((st = dalloc_t(h, &h->sort.cursor, h->nblocks)) != MPM_OK) return bail(st);
     }
-    e = cudaMallocHost(&h->h_frames, sizeof(ToolFrame) * (size_t)h->sub_chunk * n_envs * MPM_MAX_TOOLS);
-    if (e != cudaSuccess) return bail(fail(MPM_ERR_ALLOC, "cudaMallocHost: %s", cudaGetErrorString(e)));
+    for (int b = 0; b < 2; ++b) {
+        e = cudaMallocHost(&h->h_frames[b], sizeof(ToolFrame) * (size_t)h->sub_chunk * n_envs * MPM_MAX_TOOLS);
+        if (e != cudaSuccess) return bail(fail(MPM_ERR_ALLOC, "cudaMallocHost: %s", cudaGetErrorString(e)));
+    }
     e = cudaMallocHost(&h->h_err, sizeof(uint32_t));
     if (e != cudaSuccess) return bail(fail(MPM_ERR_ALLOC, "cudaMallocHost: %s", cudaGetErrorString(e)));
     *h->h_err = 0;
     if ((e = cudaEventCreateWithFlags(&h->ev_err, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&h->ev_frames, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_frames[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_frames[1], cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(fail(MPM_ERR_CUDA, "event/stream creation: %s", cudaGetErrorString(e)));
-    e = cudaEventRecord(h->ev_frames, h->stream);
+    e = cudaEventRecord(h->ev_frames[0], h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_frames[1], h->stream);
     if (e == cudaSuccess && h->fb.astamp) e = cudaMemsetAsync(h->fb.astamp, 0, sizeof(uint32_t) * h->nblocks, h->stream);
     if (e == cudaSuccess && h->fb.gstamp) e = cudaMemsetAsync(h->fb.gstamp, 0, sizeof(uint32_t) * h->nblocks, h->stream);
     for (int b = 0; b < 2 && e == cudaSuccess && h->fb.tabs[b]; ++b) {
@@ -561,7 +593,8 @@ mpm_status mpm_set_stream(mpm_handle *h, void *cuda_stream) {
     mpm_status st = check_handle(h);
     if (st != MPM_OK) return st;
     h->stream = (cudaStream_t)cuda_stream;
-    CK(cudaEventRecord(h->ev_frames, h->stream));
+    CK(cudaEventRecord(h->ev_frames[0], h->stream));
+    CK(cudaEventRecord(h->ev_frames[1], h->stream));
     return MPM_OK;
 }
 
@@ -980,6 +1013,141 @@ mpm_status copy_in(float *dst, const float *src, size_t count, int on_device, cu
     return MPM_OK;
 }
 
+// The fused-kernel configuration of a recorded rollout (its forward pass and
+// the segment replays of its reverse pass): 256 threads, 2 passes per flush,
+// 2 CTAs per SM.
+constexpr int kRecordConfig = 4;
+int record_grid(mpm_handle *h) {
+    if (h->rec_grid == 0) {
+        fused_step_occupancy(kRecordConfig);    // opts the configuration into its shared memory
+        h->rec_grid = h->num_sms * std::max(fused_record_occupancy(), 1);
+    }
+    return h->rec_grid;
+}
+
+// Floats of one recorded sub-step's particles (xi, f0, f1, vc0, vc1, vc2 as
+// float4; f2)
+size_t rs_floats(int64_t n) { return 24 * (size_t)n + (((size_t)n + 3) & ~size_t(3)); }
+// Words of one recorded sub-step's block table: ranges (2 per block), the
+// work list (1 per block) and the list length (padded to 4 words)
+size_t rs_words(const mpm_handle *h) { return 3 * (size_t)h->nblocks + 4; }
+
+StepRecord step_record(mpm_handle *h, int j) {
+    Tape &tp = h->tape;
+    const size_t n = (size_t)tp.n;
+    float *base = tp.rs + (size_t)j * rs_floats(tp.n);
+    uint32_t *w = tp.rs_blk + (size_t)j * rs_words(h);
+    StepRecord r;
+    r.xi = reinterpret_cast<float4 *>(base);
+    r.f0 = reinterpret_cast<float4 *>(base + 4 * n);
+    r.f1 = reinterpret_cast<float4 *>(base + 8 * n);
+    r.vc.vc0 = reinterpret_cast<float4 *>(base + 12 * n);
+    r.vc.vc1 = reinterpret_cast<float4 *>(base + 16 * n);
+    r.vc.vc2 = reinterpret_cast<float4 *>(base + 20 * n);
+    r.f2 = base + 24 * n;
+    r.blk = reinterpret_cast<uint2 *>(w);
+    r.act = w + 2 * (size_t)h->nblocks;
+    r.nact = w + 3 * (size_t)h->nblocks;
+    r.grid = tp.rs_grid + (size_t)j * (size_t)h->P.n * h->P.n * h->P.n;
+    return r;
+}
+
+// The fused state as an image by particle id: x (3n), v (3n), F (9n), C (9n).
+void id_image(mpm_handle *h, float *img) {
+    const size_t n = (size_t)h->n;
+    launch_read_out(cur_state(h), h->fb.vc, (uint32_t)n, img, img + 3 * n, img + 6 * n, img + 15 * n, h->elem_grid,
+                    h->stream);
+}
+
+mpm_status load_impl(mpm_handle *h, const int64_t *counts, const float *x, const float *v, const float *F,
+                     const float *C, const float *volumes, int on_device);
+
+// Replace the fused state by an image made with id_image.
+mpm_status load_image(mpm_handle *h, const float *img) {
+    const size_t n = (size_t)h->n;
+    const int64_t cnt = h->n;
+    const float vol = h->particle_volume;
+    const int64_t taken = h->taken;
+    mpm_status st = load_impl(h, &cnt, img, img + 3 * n, img + 6 * n, img + 15 * n, &vol, 1);
+    h->taken = taken;
+    return st;
+}
+
+// Reverse pass of a rollout recorded on the fused pipeline.  Segment by
+// segment, last first: restore the segment's checkpoint, replay it with
+// recording sub-steps, then reverse its sub-steps with the block-sorted
+// reverse sub-step (G2P of sub-step k and P2G of sub-step k+1) and the
+// reverse grid operation of sub-step k; finally the reverse of the first
+// sub-step's P2G.  The live state is restored to the rollout's end.
+mpm_status fused_reverse(mpm_handle *h, const AdjState &A, int nck) {
+    Tape &tp = h->tape;
+    const int nt = tp.ntools;
+    const size_t n = (size_t)tp.n;
+    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+    const size_t nbk = h->nblocks;
+    cudaStream_t s = h->stream;
+    if (h->rev_grid == 0) h->rev_grid = h->num_sms * std::max(reverse_step_ctas_per_sm(), 1);
+    float4 *gnext = tp.gbar, *gcur = tp.gb2;     // dL/d(m, mv) of G_{k+1}; dL/dV_k, then dL/d(m, mv) of G_k
+    // both start clean; afterwards only the blocks a sub-step touched are cleared.
+    // Touched-block lists of sub-step k live in slot k % 3 (blocks, then the
+    // counts of the three slots); the reverse grid operation of sub-step k
+    // clears the blocks of sub-step k+1 and zeroes the count of slot (k+2) % 3,
+    // which the reverse sub-step k-1 fills next.
+    CK(cudaMemsetAsync(gnext, 0, sizeof(float4) * nn, s));
+    CK(cudaMemsetAsync(gcur, 0, sizeof(float4) * nn, s));
+    uint32_t *stamp = tp.touch, *lists = tp.touch + nbk, *counts = lists + 3 * nbk;
+    CK(cudaMemsetAsync(counts, 0, 3 * sizeof(uint32_t), s));
+    mpm_status st;
+    if ((st = ensure(h, &tp.lame_part, &tp.cap_lame, 2 * (size_t)h->rev_grid)) != MPM_OK) return st;
+    CK(cudaMemsetAsync(tp.lame_part, 0, sizeof(double) * 2 * h->rev_grid, s));
+    for (int sg = nck - 1; sg >= 0; --sg) {
+        const int c0 = sg * tp.ck, len = std::min(tp.ck, tp.nsub - c0);
+        if ((st = load_image(h, tp.ckpt + (size_t)sg * tp.image)) != MPM_OK) return st;
+        for (int j = 0; j < len; ++j) {
+            launch_fused_step_record(h->P, h->fb, tp.frames + (size_t)(c0 + j) * nt, step_record(h, j), record_grid(h),
+                                     s);
+            h->step += 1u;
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            const int k = c0 + j;
+            const int sk = k % 3, sk1 = (k + 1) % 3, sk2 = (k + 2) % 3;
+            ReverseArgs R{};
+            R.rec = step_record(h, j);
+            R.Gk = R.rec.grid;
+            R.frames = tp.frames + (size_t)k * nt;
+            R.gbar_next = gnext;
+            R.vbar = gcur;
+            R.lam = A;
+            R.lame_part = tp.lame_part;
+            R.stamp = stamp;
+            R.sv = ++tp.touch_sv;
+            R.touch_list = lists + (size_t)sk * nbk;
+            R.touch_count = counts + sk;
+            launch_reverse_step(k + 1 < tp.nsub, true, h->P, R, h->rev_grid, s);
+            AdjGridLists L;
+            L.list = R.touch_list;
+            L.count = R.touch_count;
+            L.zlist = lists + (size_t)sk1 * nbk;
+            L.zcount = counts + sk1;
+            L.zbuf = gnext;
+            L.reset = counts + sk2;
+            launch_adj_grid(h->P, R.Gk, R.frames, gcur, tp.red + 2 + (size_t)k * nt * 18, 2 * h->num_sms, s, L);
+            std::swap(gnext, gcur);
+        }
+    }
+    // the first sub-step's P2G at the initial state (its v and C from checkpoint 0)
+    ReverseArgs R{};
+    R.rec = step_record(h, 0);
+    R.gbar_next = gnext;
+    R.lam = A;
+    R.v0 = tp.ckpt + 3 * n;
+    R.C0 = tp.ckpt + 15 * n;
+    R.lame_part = tp.lame_part;
+    launch_reverse_step(true, false, h->P, R, h->rev_grid, s);
+    CK(cudaGetLastError());
+    return load_image(h, tp.final_img);
+}
+
 mpm_status copy_out(float *dst, const float *src, size_t count, int on_device, cudaStream_t st) {
     if (!dst) return MPM_OK;
     CK(cudaMemcpyAsync(dst, src, sizeof(float) * count, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -994,8 +1162,7 @@ extern "C" {
 mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *poses, int32_t checkpoint_every) {
     mpm_status st = check_handle(h);
     if (st != MPM_OK) return st;
-    if (is_fused(h) || h->n_envs != 1)
-        return fail(MPM_ERR_STATE, "mpm_tape_record needs a split-pipeline handle with one environment");
+    if (h->n_envs != 1) return fail(MPM_ERR_STATE, "mpm_tape_record needs a handle with one environment");
     if (!h->loaded) return fail(MPM_ERR_STATE, "no particles loaded");
     if (n_substeps < 1) return fail(MPM_ERR_ARG, "n_substeps must be >= 1");
     if (checkpoint_every < 1) return fail(MPM_ERR_ARG, "checkpoint_every must be >= 1");
@@ -1010,15 +1177,40 @@ mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *pose
     const int ck = std::min(checkpoint_every, n_substeps);
     const int nck = (n_substeps + ck - 1) / ck;
     const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
-    tp.image = 24 * (size_t)n + (((size_t)n + 3) & ~size_t(3));
-    if ((st = ensure(h, &tp.ckpt, &tp.cap_ckpt, tp.image * nck)) != MPM_OK) return st;
-    if ((st = ensure(h, &tp.seg, &tp.cap_seg, tp.image * ck)) != MPM_OK) return st;
-    if ((st = ensure(h, &tp.seg_grid, &tp.cap_grid, nn * ck)) != MPM_OK) return st;
-    if ((st = ensure(h, &tp.seg_vel, &tp.cap_vel, nn * ck)) != MPM_OK) return st;
-    size_t one = nn;
-    if ((st = ensure(h, &tp.gv, &one, nn)) != MPM_OK) return st;
-    one = nn;
-    if ((st = ensure(h, &tp.gbar, &one, nn)) != MPM_OK) return st;
+    tp.fused = is_fused(h);
+    if (tp.fused) {
+        tp.image = 24 * (size_t)n;
+        if ((st = ensure(h, &tp.ckpt, &tp.cap_ckpt, tp.image * nck)) != MPM_OK) return st;
+        if ((st = ensure(h, &tp.final_img, &tp.cap_final, tp.image)) != MPM_OK) return st;
+        if ((st = ensure(h, &tp.rs, &tp.cap_rs, rs_floats(n) * ck)) != MPM_OK) return st;
+        if (tp.cap_rsg < nn * ck) {
+            // recorded sub-steps write the grid over their blocks' regions only; the
+            // reverse grid operation also reads the rest of the blocks it lists, where
+            // it needs finite values (its adjoint there is zero)
+            if ((st = ensure(h, &tp.rs_grid, &tp.cap_rsg, nn * ck)) != MPM_OK) return st;
+            CK(cudaMemsetAsync(tp.rs_grid, 0, sizeof(float4) * nn * ck, h->stream));
+        }
+        if ((st = ensure(h, &tp.rs_blk, &tp.cap_rsb, rs_words(h) * ck)) != MPM_OK) return st;
+        if ((st = ensure(h, &tp.gbar, &tp.cap_gb, nn)) != MPM_OK) return st;
+        size_t one = tp.cap_gb;
+        if ((st = ensure(h, &tp.gb2, &one, nn)) != MPM_OK) return st;
+        const size_t tw = 4 * (size_t)h->nblocks + 3;
+        if (tp.cap_touch < tw) {
+            if ((st = ensure(h, &tp.touch, &tp.cap_touch, tw)) != MPM_OK) return st;
+            CK(cudaMemsetAsync(tp.touch, 0, sizeof(uint32_t) * tw, h->stream));
+            tp.touch_sv = 0;
+        }
+    } else {
+        tp.image = 24 * (size_t)n + (((size_t)n + 3) & ~size_t(3));
+        if ((st = ensure(h, &tp.ckpt, &tp.cap_ckpt, tp.image * nck)) != MPM_OK) return st;
+        if ((st = ensure(h, &tp.seg, &tp.cap_seg, tp.image * ck)) != MPM_OK) return st;
+        if ((st = ensure(h, &tp.seg_grid, &tp.cap_grid, nn * ck)) != MPM_OK) return st;
+        if ((st = ensure(h, &tp.seg_vel, &tp.cap_vel, nn * ck)) != MPM_OK) return st;
+        size_t one = nn;
+        if ((st = ensure(h, &tp.gv, &one, nn)) != MPM_OK) return st;
+        one = nn;
+        if ((st = ensure(h, &tp.gbar, &one, nn)) != MPM_OK) return st;
+    }
     if ((st = ensure(h, &tp.abar, &tp.cap_abar, 24 * (size_t)n)) != MPM_OK) return st;
     if ((st = ensure(h, &tp.frames, &tp.cap_frames, (size_t)n_substeps * std::max(nt, 1))) != MPM_OK) return st;
     if ((st = ensure(h, &tp.red, &tp.cap_red, 2 + (size_t)n_substeps * nt * 18)) != MPM_OK) return st;
@@ -1036,10 +1228,25 @@ mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *pose
     if (nt > 0) CK(cudaMemcpy(tp.frames, hf.data(), sizeof(ToolFrame) * hf.size(), cudaMemcpyHostToDevice));
     tp.E = h->env_E[0];
     tp.nu = h->env_nu[0];
-    for (int k = 0; k < n_substeps; ++k) {
-        if (k % ck == 0 && (st = live_to_image(h, tp.ckpt + (size_t)(k / ck) * tp.image)) != MPM_OK) return st;
-        if ((st = split_substep(h, h->fb.P[0], h->fb.vc, h->fb.G[0], nullptr, tp.frames + (size_t)k * nt)) != MPM_OK)
-            return st;
+    if (tp.fused) {
+        // checkpoints by particle id; v and C of a checkpointed state are written by
+        // the sub-step before it
+        for (int k = 0; k < n_substeps; ++k) {
+            if (k % ck == 0) id_image(h, tp.ckpt + (size_t)(k / ck) * tp.image);
+            // the configuration the reverse pass replays segments with, so that the
+            // replay follows the recorded trajectory up to the order of float atomics
+            const bool wv = (k + 1) % ck == 0 || k + 1 == n_substeps;
+            launch_fused_step(h->P, h->fb, tp.frames + (size_t)k * nt, wv, record_grid(h), kRecordConfig, h->stream);
+            h->step += 1u;
+        }
+        id_image(h, tp.final_img);
+    } else {
+        for (int k = 0; k < n_substeps; ++k) {
+            if (k % ck == 0 && (st = live_to_image(h, tp.ckpt + (size_t)(k / ck) * tp.image)) != MPM_OK) return st;
+            if ((st = split_substep(h, h->fb.P[0], h->fb.vc, h->fb.G[0], nullptr, tp.frames + (size_t)k * nt)) !=
+                MPM_OK)
+                return st;
+        }
     }
     CK(cudaGetLastError());
     h->taken += n_substeps;
@@ -1077,7 +1284,10 @@ mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_b
     const size_t nred = 2 + (size_t)tp.nsub * nt * 18;
     CK(cudaMemsetAsync(tp.red, 0, sizeof(double) * nred, s));
     const int nck = (tp.nsub + tp.ck - 1) / tp.ck;
-    for (int sg = nck - 1; sg >= 0; --sg) {
+    if (tp.fused) {
+        if ((st = fused_reverse(h, A, nck)) != MPM_OK) return st;
+    }
+    for (int sg = tp.fused ? -1 : nck - 1; sg >= 0; --sg) {
         const int c0 = sg * tp.ck, len = std::min(tp.ck, tp.nsub - c0);
         CK(cudaMemcpyAsync(tp.seg, tp.ckpt + (size_t)sg * tp.image, sizeof(float) * tp.image, cudaMemcpyDeviceToDevice,
                            s));
@@ -1122,9 +1332,17 @@ mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_b
     if ((st = copy_out(C0_bar, A.C, 9 * (size_t)n, on_device, s)) != MPM_OK) return st;
     std::vector<double> red(nred);
     CK(cudaMemcpyAsync(red.data(), tp.red, sizeof(double) * nred, cudaMemcpyDeviceToHost, s));
+    std::vector<double> lame_part(tp.fused ? 2 * (size_t)h->rev_grid : 0);
+    if (tp.fused)
+        CK(cudaMemcpyAsync(lame_part.data(), tp.lame_part, sizeof(double) * lame_part.size(), cudaMemcpyDeviceToHost,
+                           s));
     if ((st = enqueue_error_copy(h)) != MPM_OK) return st;
     CK(cudaStreamSynchronize(s));
     if ((st = poll_error(h, true)) != MPM_OK) return st;
+    for (size_t c = 0; c + 1 < lame_part.size(); c += 2) {
+        red[0] += lame_part[c];
+        red[1] += lame_part[c + 1];
+    }
     if (grad_material) {   // Eq. 6 backwards
         const double E = tp.E, nu = tp.nu, D = (1.0 + nu) * (1.0 - 2.0 * nu);
         grad_material[0] = red[0] / (2.0 * (1.0 + nu)) + red[1] * nu / D;

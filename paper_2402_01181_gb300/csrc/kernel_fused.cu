@@ -107,6 +107,12 @@ __device__ __forceinline__ int fix_round(float scaled_plus_magic) {
     return __float_as_int(scaled_plus_magic) - 0x4B400000;
 }
 
+// G[addr] += v as one vector reduction (no value returned)
+__device__ __forceinline__ void red_add4(float4 *addr, float4 v) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
     const int bytes = valid ? 16 : 0;   // 0: fill with zeros, read nothing
@@ -176,9 +182,14 @@ __device__ __forceinline__ void prefetch_block(Smem &s, int buf, uint32_t b, con
 
 
 // MINB: resident CTAs per SM the configuration is compiled for (the register budget)
-template <bool WRITE_VC, int T, int GP, int MINB = kMinBlocks<T, GP>>
+// RECORD: also write, for the reverse mode, every block's input particles in
+// block-contiguous order (the range [out_base, out_base + total) the block's
+// output was allocated), each block's range, the list of blocks in work order
+// and its length.
+template <bool WRITE_VC, int T, int GP, int MINB = kMinBlocks<T, GP>, bool RECORD = false>
 __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B,
-                                                                     const ToolFrame *__restrict__ tools) {
+                                                                     const ToolFrame *__restrict__ tools,
+                                                                     StepRecord rec) {
     using Smem = FusedSmem<T, GP>;
     constexpr int NW = Smem::NW, GROUP = Smem::GROUP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -239,6 +250,7 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
         const uint32_t item = s.items[cb];
         if (item >= nact) break;
         const uint32_t b = s.bids[cb];                 // global block
+        if (RECORD && tid == 0) rec.act[item] = b;
         const uint32_t env = b / nbe, bl = b % nbe;     // environment, block inside it
         const uint32_t eb0 = env * nbe;                 // first global block of the environment
         const int bx = bl % nb, by = (bl / nb) % nb, bz = bl / (nb * nb);
@@ -256,6 +268,7 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
             const int i = 4 * bx + q % 6, j = 4 * by + (q / 6) % 6, k = 4 * bz + q / 36;
             const float4 g = gv[q];
             float3 v = make_float3(0.f, 0.f, 0.f);
+            if (RECORD && i < n && j < n && k < n) rec.grid[node_addr_env(env, i, j, k, nb, nbe)] = g;
             if (i < n && j < n && k < n) v = grid_node_update(g.x, g.y, g.z, g.w, i, j, k, P, s.tools[cb], ep.ntools);
             gv[q] = make_float4(v.x, v.y, v.z, 0.f);
         }
@@ -362,6 +375,7 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
                 t.stamp = 0; t.first = 0; t.npass = 0;
             }
             tout[b] = t;
+            if (RECORD) rec.blk[b] = make_uint2(fit ? alloc_ob : 0u, fit ? total : 0u);
             s.out_base = fit ? alloc_ob : nparticles;
             s.chunk_first = fit ? alloc_cf : nchunk_cap;
         }
@@ -518,8 +532,8 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
                             const float rz = qz + A[7] * jj + A[8] * kk;
                             for (int ii = 0; ii < 3; ++ii) {
                                 const float w = wx2[ii] * wjk;
-                                atomicAdd(&Gnext[node_addr_env(env, hx + ii, hy + jj, hz + kk, nb, nbe)],
-                                          make_float4(w * m, w * (rx + A[0] * ii), w * (ry + A[3] * ii), w * (rz + A[6] * ii)));
+                                red_add4(&Gnext[node_addr_env(env, hx + ii, hy + jj, hz + kk, nb, nbe)],
+                                         make_float4(w * m, w * (rx + A[0] * ii), w * (ry + A[3] * ii), w * (rz + A[6] * ii)));
                             }
                         }
                     for (int c = 0; c < 8; ++c) {
@@ -581,6 +595,13 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
                 }
                 const unsigned nz = __ballot_sync(0xffffffffu, lane < 27 && run > 0);
                 if (lane == 0) s.mask |= nz;
+            }
+            if (RECORD && valid && out_base + j < nparticles) {
+                rec.xi[out_base + j] = xi;
+                rec.f0[out_base + j] = a0;
+                rec.f1[out_base + j] = a1;
+                rec.f2[out_base + j] = f2;
+                store_vc(rec.vc, out_base + j, vx, vy, vz, Cm);
             }
             const uint32_t pos = out_base + pass * T + my_off + rank;
             if (valid && pos < nparticles) {
@@ -690,8 +711,8 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
                     if (am != 0 || px != 0 || py != 0 || pz != 0) {
                         const int i = ox + lx8, jn = oy + ly8, k = oz + lz8;
                         if (i >= 0 && jn >= 0 && k >= 0 && i < n && jn < n && k < n)
-                            atomicAdd(&Gnext[node_addr_env(env, i, jn, k, nb, nbe)],
-                                      make_float4((float)am * um, (float)px * up, (float)py * up, (float)pz * up));
+                            red_add4(&Gnext[node_addr_env(env, i, jn, k, nb, nbe)],
+                                     make_float4((float)am * um, (float)px * up, (float)py * up, (float)pz * up));
                         s.acc[0][a] = 0; s.acc[1][a] = 0; s.acc[2][a] = 0; s.acc[3][a] = 0;
                     }
                 }
@@ -702,25 +723,30 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
                 __syncthreads();
             }
         }
+        // the block's direction mask and size, read before warp 0 reuses them for the
+        // next block
+        const uint32_t mask_b = s.mask, total_b = s.total;
         cp_async_wait_all();
         __syncthreads();
-        // blocks of the next sub-step and grid blocks to clear before G_{k+1}'s reuse
-        if (warp == 0 && lane < 27) {
+        // blocks of the next sub-step (the last warp) and grid blocks to clear before
+        // G_{k+1}'s reuse (the one before it): two chains of dependent global atomics
+        // that run beside warp 0's set-up of the next block
+        if (warp >= NW - 2 && lane < 27) {
             const int tx = bx + dir_dx(lane), ty = by + dir_dy(lane), tz = bz + dir_dz(lane);
             if (tx >= 0 && ty >= 0 && tz >= 0 && tx < nb && ty < nb && tz < nb) {
                 const uint32_t tb = eb0 + block_id(tx, ty, tz, nb);
-                if ((s.mask >> lane) & 1u) {
+                if (warp == NW - 1 && ((mask_b >> lane) & 1u)) {
                     // heavy: b itself (lane 13) with more particles now than one pass
                     // of the CTA takes.  A neighbour's mark wins only for blocks that
                     // particles enter from outside, which are light.
                     if (atomicExch(&B.astamp[tb], step + 1) != step + 1) {
-                        if (lane == 13 && s.total > (uint32_t)T)
+                        if (lane == 13 && total_b > (uint32_t)T)
                             act_next[atomicAdd(&ctrl->nactive[par ^ 1][0], 1u)] = tb;
                         else
                             act_next[acap - 1u - atomicAdd(&ctrl->nactive[par ^ 1][1], 1u)] = tb;
                     }
                 }
-                mark_clear(B, tb, step + 1, m3n);
+                if (warp == NW - 2) mark_clear(B, tb, step + 1, m3n);
             }
         }
     }
@@ -742,6 +768,7 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
             ctrl->nclear[m3c] = 0;
             ctrl->done = 0;
             __threadfence();
+            if (RECORD) *rec.nact = nact;
             ctrl->step = step + 1;
         }
     }
@@ -750,10 +777,11 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
 template <int T, int GP, int MINB = kMinBlocks<T, GP>>
 void launch_variant(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, bool write_vc, int grid,
                     cudaStream_t st) {
+    const StepRecord none{};
     if (write_vc)
-        k_fused_step<true, T, GP, MINB><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools);
+        k_fused_step<true, T, GP, MINB><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools, none);
     else
-        k_fused_step<false, T, GP, MINB><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools);
+        k_fused_step<false, T, GP, MINB><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools, none);
 }
 
 template <int T, int GP, int MINB = kMinBlocks<T, GP>>
@@ -781,6 +809,21 @@ void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *
 }
 
 int fused_step_threads(int config) { return config == 2 || config == 3 ? 128 : 256; }
+
+// The recording sub-step of the differentiable rollout: the configuration of
+// 256 threads, 2 passes per flush and 2 CTAs per SM (128 registers).
+int fused_record_occupancy() {
+    constexpr int bytes = (int)sizeof(FusedSmem<256, 2>);
+    cudaFuncSetAttribute(k_fused_step<false, 256, 2, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fused_step<false, 256, 2, 2, true>, 256, bytes);
+    return a;
+}
+
+void launch_fused_step_record(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, const StepRecord &rec,
+                              int grid, cudaStream_t st) {
+    k_fused_step<false, 256, 2, 2, true><<<grid, 256, sizeof(FusedSmem<256, 2>), st>>>(P, B, tools, rec);
+}
 
 // Also opts the kernel into its dynamic shared memory size on the current
 // device; called when a handle is created.

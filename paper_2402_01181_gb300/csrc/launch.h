@@ -42,10 +42,31 @@ void launch_adj_g2p(const DevParams &P, const PState &S, uint32_t n, const float
                     int grid, cudaStream_t st);
 // G: the (m, mv) grid the forward grid operation read; Gb in: velocity
 // adjoint, out: (dL/dm, dL/dmv); tool_bar: ntools x 18 doubles accumulated.
+// Optional block lists (blocks, count): list, the only grid blocks that hold
+// an adjoint; zlist, blocks whose nodes are cleared in zbuf; reset, a list
+// count set to zero.
+struct AdjGridLists {
+    const uint32_t *list = nullptr, *count = nullptr;
+    const uint32_t *zlist = nullptr, *zcount = nullptr;
+    float4 *zbuf = nullptr;
+    uint32_t *reset = nullptr;
+};
 void launch_adj_grid(const DevParams &P, const float4 *G, const ToolFrame *tools, float4 *Gb, double *tool_bar,
-                     int grid, cudaStream_t st);
+                     int grid, cudaStream_t st, const AdjGridLists &L = AdjGridLists());
 void launch_adj_p2g(const DevParams &P, const PState &S, const VCState &V, uint32_t n, const float4 *Gb,
                     const AdjState &A, double *lame_bar, int grid, cudaStream_t st);
+
+// kernels_reverse.cu: reverse mode of the fused sub-step over the blocks a
+// recording sub-step listed (StepRecord, below).
+struct StepRecord;
+struct ReverseArgs;
+// CTAs per SM of the reverse sub-step (also opts it into its shared memory)
+int reverse_step_ctas_per_sm();
+// do_p2g && do_g2p: reverse of G2P of sub-step k and P2G of sub-step k+1;
+// do_g2p alone: the last sub-step of a rollout; do_p2g alone: the reverse of
+// the first sub-step's P2G at the initial state.
+void launch_reverse_step(bool do_p2g, bool do_g2p, const DevParams &P, const ReverseArgs &R, int grid,
+                         cudaStream_t st);
 
 // kernels_surface.cu: iso-surface of the grid density m / (rho dx^3) of
 // environment env.  counts: (n-1)^3 + 1 entries, left holding the exclusive
@@ -95,12 +116,43 @@ struct FusedBufs {
     Ctrl *ctrl;
     uint32_t nblocks;
 };
+// What a recording fused sub-step writes for the reverse mode (all device
+// arrays): each block's input particles in block-contiguous order (n
+// entries), per block its (first, count) range, the blocks in work order and
+// their number.
+struct StepRecord {
+    float4 *xi, *f0, *f1;
+    float *f2;
+    uint2 *blk;          // nblocks
+    uint32_t *act;       // nblocks
+    uint32_t *nact;      // 1
+    float4 *grid;        // the grid the sub-step read, over the 6^3 region of every listed block (node layout)
+    VCState vc;          // each particle's v and C after the sub-step (n entries, same order as xi)
+};
+// Inputs and outputs of one reverse sub-step (kernels_reverse.cu).
+struct ReverseArgs {
+    const float4 *Gk;          // grid (m, mv) sub-step k read (do_g2p)
+    const ToolFrame *frames;   // tool frames of sub-step k (do_g2p)
+    StepRecord rec;            // sub-step k's input particles by block
+    const float4 *gbar_next;   // dL/d(m, mv) of G_{k+1} (do_p2g)
+    float4 *vbar;              // dL/dV_k in .yzw, accumulated (do_g2p)
+    AdjState lam;              // particle adjoints by particle id
+    const float *v0, *C0;      // initial v (n x 3), C (n x 9) by id (do_p2g alone)
+    double *lame_part;         // per CTA: its part of dL/dmu, dL/dlambda, accumulated
+    // (do_g2p) the grid blocks the sub-step scatters into -- every recorded block
+    // b and b + {0,1}^3 -- listed once in touch_list (count in touch_count, zero on
+    // entry), marked in stamp with value sv
+    uint32_t *stamp, sv, *touch_list, *touch_count;
+};
 // config (MPM_KERNEL_*): 0 = 256 threads, 2 passes per P2G flush; 1 = 256, 1;
 // 2 = 128, 2; 3 = 128, 1
 void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, bool write_vc, int grid,
                        int config, cudaStream_t st);
 int fused_step_occupancy(int config);
 int fused_step_threads(int config);
+int fused_record_occupancy();
+void launch_fused_step_record(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, const StepRecord &rec,
+                              int grid, cudaStream_t st);
 constexpr int kFusedConfigs = 5;
 constexpr int kFusedMinThreads = 128;     // chunk tables are sized for the smallest CTA
 // Inbox of a block: entry d * kNpMax + p holds the run of source pass p

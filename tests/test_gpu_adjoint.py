@@ -11,6 +11,8 @@ Rollouts of many sub-steps compare the summed gradients at 1e-2 (two tools,
 gaps of ~1e-5 m, while FP32 positions near 0.5 resolve 6e-8 m and carry
 the rounding of hundreds of sub-steps), and the oracle's own central
 differences confirm the GPU gradient."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -30,9 +32,16 @@ def M():
     return mpm
 
 
-def _sim(M, prm, n):
+PIPES = ("split", "fused")
+
+
+def _pipe(M, name):
+    return M.MPM_PIPELINE_FUSED if name == "fused" else M.MPM_PIPELINE_SPLIT
+
+
+def _sim(M, prm, n, pipe="split"):
     cfg = M.make_config(prm.n_grid, prm.dt, prm.E, prm.nu, prm.rho, gravity=tuple(prm.gravity), bound=prm.bound,
-                        theta=prm.theta, friction=prm.friction, pipeline=M.MPM_PIPELINE_SPLIT, max_particles=n)
+                        theta=prm.theta, friction=prm.friction, pipeline=_pipe(M, pipe), max_particles=n)
     return M.Sim(cfg)
 
 
@@ -40,11 +49,12 @@ def _f32_state(st):
     return {k: getattr(st, k).astype(np.float32) for k in ("x", "v", "F", "C")}
 
 
-def test_single_substep_adjoint_matches_oracle(M):
+@pytest.mark.parametrize("pipe", PIPES)
+def test_single_substep_adjoint_matches_oracle(M, pipe):
     import torch
     prm, st, tools, p0, p1 = AP._scene()
     s32 = _f32_state(st)
-    sim = _sim(M, prm, st.n)
+    sim = _sim(M, prm, st.n, pipe)
     sim.load(s32["x"], prm.V0, s32["v"], s32["F"], s32["C"])
     for t, tool in enumerate(tools):
         sim.set_tool(t, p0[t], tool.shape)
@@ -80,7 +90,8 @@ def test_single_substep_adjoint_matches_oracle(M):
         assert np.abs(got - ref).max() <= 2e-3 * np.abs(ref).max(), (t, got, ref)
 
 
-def test_rollout_gradients_match_oracle(M):
+@pytest.mark.parametrize("pipe", PIPES)
+def test_rollout_gradients_match_oracle(M, pipe):
     """30 sub-steps with two moving tools, checkpoints every 8 (a short last
     segment), loss = mean |x(T) - target|^2, through torch.autograd."""
     import torch
@@ -92,7 +103,7 @@ def test_rollout_gradients_match_oracle(M):
     rng = np.random.default_rng(22)
     target = (st.x + 0.01 * rng.normal(size=st.x.shape)).astype(np.float32)
     dev = torch.device("cuda")
-    sim = _sim(M, prm, st.n)
+    sim = _sim(M, prm, st.n, pipe)
     for t, tool in enumerate(tools):
         sim.set_tool(t, p0[t], tool.shape)
     E = torch.tensor(prm.E, dtype=torch.float64, requires_grad=True)
@@ -172,16 +183,19 @@ def test_slab30k_rollout_gradient_against_oracle_and_differences(M):
     assert abs(nu.grad.item() - fdn) <= 5e-2 * abs(fdn), (nu.grad.item(), fdn)
 
 
-def test_tape_contract(M):
+@pytest.mark.parametrize("pipe", PIPES)
+def test_tape_contract(M, pipe):
     import torch
     sc = scenes.cube8k()
-    fused = M.sim_from_scene(sc)
     poses = np.zeros((3, 0, 6))
-    with pytest.raises(M.MPMError) as e:
-        fused.tape_record(poses, 1)
+    cfg = M.make_config(sc.n_grid, sc.dt, sc.E, sc.nu, sc.rho, n_envs=2, max_particles=sc.n)
+    batched = M.Sim(cfg)
+    batched.load_batch([sc.x[:100], sc.x[100:200]], [sc.particle_volume] * 2)
+    with pytest.raises(M.MPMError) as e:           # one environment only
+        batched.tape_record(poses, 1)
     assert e.value.status == M.MPM_ERR_STATE
-    fused.close()
-    sim = M.sim_from_scene(sc, pipeline=M.MPM_PIPELINE_SPLIT)
+    batched.close()
+    sim = M.sim_from_scene(sc, pipeline=_pipe(M, pipe))
     with pytest.raises(M.MPMError) as e:
         sim.tape_backward(torch.zeros((sc.n, 3), device="cuda"))
     assert e.value.status == M.MPM_ERR_STATE
@@ -200,15 +214,11 @@ def test_tape_contract(M):
     sim.close()
 
 
-def test_config5_full_size_gradients_match_oracle(M):
-    """The full differentiable workload the benchmark times: the 30K slab
-    over 500 sub-steps (the capsule descends, touches near sub-step 100 and
-    presses 2 cm in), checkpoints every 50; the target from an FP64 oracle
-    rollout with E = 1.2e4, nu = 0.33 and shifted poses.  The GPU loss and
-    its gradients with respect to E, nu and all 500 x 6 pose entries against
-    the oracle's adjoint."""
-    import torch
-    from paper_2402_01181_gb300 import autodiff
+@functools.lru_cache(maxsize=1)
+def _config5_oracle():
+    """The differentiable workload's FP32 target (an FP64 oracle rollout with
+    E = 1.2e4, nu = 0.33 and shifted poses) and the oracle's loss and
+    gradients at the workload's own parameters."""
     case = scenes.slab30k_diff()
     sc = case.scene
     prm = O.OracleParams.from_scene(sc)
@@ -218,8 +228,28 @@ def test_config5_full_size_gradients_match_oracle(M):
     tf, nt = O.rollout_frames(sc.tools, case.pose_init, case.target_poses, prm.dt)
     O.run(tprm, tgt_state, case.poses.shape[0], tf, nt)
     target = tgt_state.x.astype(np.float32)
+    ref = O.rollout_loss_and_gradients(prm, st0, sc.tools, case.pose_init, case.poses, target.astype(np.float64),
+                                       checkpoint=case.checkpoint)
+    return case, target, ref
+
+
+@pytest.mark.parametrize("pipe", PIPES)
+def test_config5_full_size_gradients_match_oracle(M, pipe):
+    """The full differentiable workload the benchmark times: the 30K slab
+    over 500 sub-steps (the capsule descends, touches near sub-step 100 and
+    presses 2 cm in), checkpoints every 50.  The GPU loss and its gradients
+    with respect to E, nu and all 500 x 6 pose entries against the oracle's
+    adjoint, end to end: the FP32 forward trajectory drifts from the FP64 one
+    over 500 sub-steps, and the loss is a mean of squared gaps of ~1e-5 m, so
+    the bar here is 3e-2 / 5e-2 (the adjoint's own arithmetic is checked at
+    1e-3, segment by segment, in the test below)."""
+    import torch
+    from paper_2402_01181_gb300 import autodiff
+    case, target, ref = _config5_oracle()
+    sc = case.scene
+    prm = O.OracleParams.from_scene(sc)
     dev = torch.device("cuda")
-    sim = M.sim_from_scene(sc, pipeline=M.MPM_PIPELINE_SPLIT, load=False)
+    sim = M.sim_from_scene(sc, pipeline=_pipe(M, pipe), load=False)
     sim.set_tool(0, case.pose_init[0], sc.tools[0].shape)
     E = torch.tensor(prm.E, dtype=torch.float64, requires_grad=True)
     nu = torch.tensor(prm.nu, dtype=torch.float64, requires_grad=True)
@@ -229,13 +259,11 @@ def test_config5_full_size_gradients_match_oracle(M):
     loss = ((xT - torch.tensor(target, device=dev)) ** 2).sum(dim=1).mean()
     loss.backward()
     sim.close()
-    ref = O.rollout_loss_and_gradients(prm, st0, sc.tools, case.pose_init, case.poses, target.astype(np.float64),
-                                       checkpoint=case.checkpoint)
-    assert abs(loss.item() - ref["loss"]) <= 2e-2 * ref["loss"], (loss.item(), ref["loss"])
-    assert abs(E.grad.item() - ref["E"]) <= 3e-2 * abs(ref["E"]), (E.grad.item(), ref["E"])
-    assert abs(nu.grad.item() - ref["nu"]) <= 3e-2 * abs(ref["nu"]), (nu.grad.item(), ref["nu"])
-    gp = P.grad.numpy()
-    assert np.abs(gp - ref["poses"]).max() <= 5e-2 * np.abs(ref["poses"]).max()
+    err = {"loss": abs(loss.item() - ref["loss"]) / ref["loss"], "E": abs(E.grad.item() - ref["E"]) / abs(ref["E"]),
+           "nu": abs(nu.grad.item() - ref["nu"]) / abs(ref["nu"]),
+           "poses": np.abs(P.grad.numpy() - ref["poses"]).max() / np.abs(ref["poses"]).max()}
+    print("config-5 end-to-end relative errors (%s):" % pipe, err)
+    assert err["loss"] <= 2e-2 and err["E"] <= 3e-2 and err["nu"] <= 3e-2 and err["poses"] <= 5e-2, err
 
 
 def _segment_errors(got, ref):
@@ -252,17 +280,31 @@ def _segment_errors(got, ref):
     return out
 
 
-def test_config5_segments_match_oracle_adjoint(M):
+@pytest.mark.parametrize("pipe", PIPES)
+def test_config5_segments_match_oracle_adjoint(M, pipe):
     """The benchmark's differentiable workload (the 30K slab, 500 sub-steps,
     checkpoints every 50) reversed one 50-sub-step segment at a time, on the
     GPU (mpm_tape_record / mpm_tape_backward from the GPU's own checkpoint
     state) and in the FP64 oracle, both seeded with the same incoming adjoint
     (the GPU's, from the segment after it; the loss gradient for the last).
     The oracle reverses each sub-step at the GPU's own forward state of that
-    sub-step, so no FP32 drift of the forward trajectory enters: what is
-    compared is the adjoint's arithmetic.  Per segment, dL/dE, dL/dnu, every
-    pose entry (against the largest entry of its coordinate in the segment)
-    and the outgoing state adjoint agree to 1e-3."""
+    sub-step -- the states of the reverse pass's replay of the segment from
+    its checkpoint -- and at the GPU's own grid (the fused pipeline's P2G
+    rounds in 32-bit fixed point), so no FP32 drift of the forward trajectory
+    and no rounding of the forward grid enters: what is compared is the
+    adjoint's arithmetic.  Per segment, dL/dE, dL/dnu and the outgoing state
+    adjoint agree to 1e-3, and so does every pose entry (against the largest
+    entry of its coordinate in the segment) on the split pipeline.
+
+    On the fused pipeline the pose gradients are reproducible only to a few
+    1e-3: the reverse pass replays each segment, and the fused forward is not
+    bit-reproducible (its per-block partial grids are added with float
+    reductions in any order, and the fixed-point arena turns a last-bit change
+    of an input into a step of 2^-22 of the group's bound), which moves nodes
+    under the capsule across the stick/slide kink of Eq. 18 from one run to
+    the next.  The test measures that spread with a second GPU run and
+    requires the pose error to stay within twice it (and within 1e-3 where
+    the spread is smaller); E, nu and the state adjoints reproduce to 1e-7."""
     import torch
     case = scenes.slab30k_diff()
     sc = case.scene
@@ -272,13 +314,13 @@ def test_config5_segments_match_oracle_adjoint(M):
     dev = torch.device("cuda")
 
     def seg_sim(state, pose_start):
-        sim = M.sim_from_scene(sc, pipeline=M.MPM_PIPELINE_SPLIT, load=False)
+        sim = M.sim_from_scene(sc, pipeline=_pipe(M, pipe), load=False)
         sim.load(state["x"], sc.particle_volume, state["v"], state["F"], state["C"])
         sim.set_tool(0, pose_start, tool.shape)
         return sim
 
     # the GPU's forward trajectory, one sub-step per recorded call
-    sim = M.sim_from_scene(sc, pipeline=M.MPM_PIPELINE_SPLIT, load=False)
+    sim = M.sim_from_scene(sc, pipeline=_pipe(M, pipe), load=False)
     sim.load(sc.x, sc.particle_volume)
     sim.set_tool(0, case.pose_init[0], tool.shape)
     states = []
@@ -297,20 +339,43 @@ def test_config5_segments_match_oracle_adjoint(M):
             "v": np.zeros((sc.n, 3), np.float32), "F": np.zeros((sc.n, 9), np.float32),
             "C": np.zeros((sc.n, 9), np.float32)}
     worst = {}
+    spreads = []
     for s in range(K // ck - 1, -1, -1):
         seg_poses = case.poses[s * ck:(s + 1) * ck]
-        sim = seg_sim(states[s * ck], starts[s])
-        sim.tape_record(seg_poses, ck)
-        g = sim.tape_backward(*[torch.tensor(seed[k], device=dev) for k in ("x", "v", "F", "C")], want_state=True)
-        sim.close()
+        runs = []
+        for _ in range(2 if pipe == "fused" else 1):
+            sim = seg_sim(states[s * ck], starts[s])
+            sim.tape_record(seg_poses, ck)
+            runs.append(sim.tape_backward(*[torch.tensor(seed[k], device=dev) for k in ("x", "v", "F", "C")],
+                                          want_state=True))
+            sim.close()
+        g = runs[0]
         got = {"E": g["E"], "nu": g["nu"], "poses": g["poses"]}
         got.update({k: g[k].cpu().numpy().astype(np.float64) for k in ("x", "v", "F", "C")})
-        seg_states = [O.State(st["x"], st["v"], st["C"], st["F"]) for st in states[s * ck:(s + 1) * ck]]
+        # the GPU's own run-to-run spread of the pose gradients (the fused forward is
+        # not bit-reproducible: see the docstring)
+        spread = 0.0
+        if len(runs) > 1:
+            scale = np.abs(g["poses"]).max(axis=0, keepdims=True)
+            spread = float((np.abs(runs[1]["poses"] - g["poses"]) / np.maximum(scale, 1e-300)).max())
+        spreads.append(spread)
+        # the states the reverse pass differentiates at: its replay of the segment from
+        # the checkpoint (a fresh load, then the recorded sub-steps one by one)
+        rep = seg_sim(states[s * ck], starts[s])
+        seg_states, seg_grids = [], []
+        for k in range(s * ck, (s + 1) * ck):
+            st = rep.read()
+            seg_states.append(O.State(st["x"], st["v"], st["C"], st["F"]))
+            seg_grids.append(rep.read_grid())
+            rep.tape_record(case.poses[k:k + 1], 1)
+        rep.close()
         ref = O.reverse_from_states(prm, seg_states, sc.tools, starts[s][None], seg_poses,
-                                    {k: seed[k].astype(np.float64) for k in ("x", "v", "F", "C")})
+                                    {k: seed[k].astype(np.float64) for k in ("x", "v", "F", "C")}, grids=seg_grids)
         err = _segment_errors(got, ref)
         for k, v in err.items():
             worst[k] = max(worst.get(k, 0.0), v)
-        assert all(v <= 1e-3 for v in err.values()), (s, err)
+        assert all(v <= 1e-3 for k, v in err.items() if k != "poses"), (s, err)
+        assert err["poses"] <= max(1e-3, 2.0 * spread), (s, err, spread)
         seed = {k: g[k].cpu().numpy() for k in ("x", "v", "F", "C")}    # the GPU's own adjoint, upstream
-    print("config-5 per-segment worst relative errors:", worst)
+    print("config-5 per-segment worst relative errors (%s):" % pipe, worst,
+          "largest run-to-run pose spread:", max(spreads))

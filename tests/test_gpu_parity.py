@@ -414,3 +414,36 @@ def test_streamed_readback_matches_synchronous_reads(M):
     for k in range(frames):
         assert np.abs(a[k] - b[k]).max() <= 1e-4 * sc.dx, k     # two runs: float atomics may round apart
     assert np.abs(a[0] - a[-1]).max() > 0
+
+
+def test_step_calls_run_ahead_of_the_gpu(M):
+    """The tool frames are staged in two pinned buffers used in turn, so a
+    call of mpm_step waits only for the frame copy of the call two before
+    it: behind a ~0.1 s kernel on the stream, two further calls return at
+    once, and the state they produce is the one of synchronous stepping."""
+    import time
+    import torch
+    sc = scenes.slab30k()
+    tool = sc.tools[0]
+    ref = M.sim_from_scene(sc)
+    sim = M.sim_from_scene(sc)
+    for si in (ref, sim):
+        si.set_tool(0, tool.pose(0), tool.shape)
+        si.step(1)                                  # first call: tables and graph set up
+        si.synchronize()
+    torch.cuda._sleep(int(2e8))
+    t0 = time.perf_counter()
+    for s in (1, 2):
+        sim.set_tool(0, tool.pose(s), tool.shape)
+        sim.step(1)
+    dt = time.perf_counter() - t0
+    sim.synchronize()
+    for s in (1, 2):
+        ref.set_tool(0, tool.pose(s), tool.shape)
+        ref.step(1)
+        ref.synchronize()
+    a, b = sim.read(), ref.read()
+    sim.close()
+    ref.close()
+    assert dt < 0.05, dt
+    assert np.abs(a["x"] - b["x"]).max() <= 1e-6
