@@ -630,6 +630,32 @@ def time_oracle_adjoint(substeps=20, checkpoint=10):
                       "backward includes the recomputation of the segments" % (substeps, sc.n, checkpoint)}
 
 
+def time_oracle_configs():
+    """The FP64 oracle (one core) on bounded samples of the other benchmark
+    workloads: particle-steps/s per workload, and env-steps/s of one batched
+    environment of the mean size."""
+    out = {}
+    for name, budget, steps in (("cube8k", 3.0, 50), ("slab30k", 3.0, 50), ("block8m", 4.0, 1)):
+        v, sample = time_oracle(name, budget, max_steps=steps)
+        out[name] = {"particle_steps_per_s": v, "sample": sample}
+    from oracle import oracle as O
+    envs = scenes.batch_envs(256, seed=0)
+    mean = float(np.mean([e.n for e in envs]))
+    env = min(envs, key=lambda e: abs(e.n - mean))
+    prm = O.OracleParams.from_scene(env)
+    st = O.State(env.x)
+    t0, done = time.perf_counter(), 0
+    while done < 20 and time.perf_counter() - t0 < 3.0:
+        frames, nt = O.frames_for_steps(env.tools, done, 1, env.dt, 1)
+        O.run(prm, st, 1, frames, nt)
+        done += 1
+    el = time.perf_counter() - t0
+    out["batch256"] = {"env_steps_per_s": done / el, "particle_steps_per_s": env.n * done / el,
+                       "sample": "%d sub-steps of one batched environment of %d particles (the mean is %.0f)"
+                                 % (done, env.n, mean)}
+    return out
+
+
 def reference_main(args):
     from paper_2402_01181_gb300 import dist as D
     world, rank, local = D.env()
@@ -698,8 +724,8 @@ def main():
     if not args.no_sweep and args.workload == "block1m" and args.pipeline == "fused":
         sweep = {}
         split_args = argparse.Namespace(**{**vars(args), "pipeline": "split"})
-        for wl, a, key in (("block8m", args, "block8m_fused"), ("block1m", split_args, "block1m_split"),
-                           ("block8m", split_args, "block8m_split")):
+        for wl, a, key in (("cube8k", args, "cube8k_fused"), ("block8m", args, "block8m_fused"),
+                           ("block1m", split_args, "block1m_split"), ("block8m", split_args, "block8m_split")):
             steps = 10 if wl == "block8m" else args.steps
             r = run_gpu_workload(wl, a, rank, device, barrier, max_over_ranks, with_e2e=False, steps=steps)
             n_units_w = r["n"] * S * r["steps"] * world
@@ -779,6 +805,7 @@ def main():
                **cpu_description()}
         if differentiable is not None:
             differentiable["oracle"] = time_oracle_adjoint()
+        cpu["other_workloads"] = time_oracle_configs()
     e2e_val = main_res["n"] * S * args.steps * world / (main_res["t_e2e_ms"] / 1e3)
     launches_per_frame = S if args.pipeline == "fused" else 3 * S
     line = {
