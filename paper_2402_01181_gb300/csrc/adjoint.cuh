@@ -60,6 +60,10 @@ __device__ __forceinline__ void tool_normal_jacobian(int kind, const float *dims
     }
 }
 
+// a[k] for a run-time k in 0..2 by selects, so that a stays in registers
+template <class T>
+__device__ __forceinline__ T pick3(const T a[3], int k) { return k == 0 ? a[0] : (k == 1 ? a[1] : a[2]); }
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -83,63 +87,88 @@ struct ThreeLanes {
     }
 };
 
+// Per-axis stencil tables of one particle: weights w, their gradients dw in
+// world units (d w / d x), and node offsets dp = (i - f) dx from the particle.
+struct StencilAxes {
+    int b[3];
+    float f[3], w[3][3], dw[3][3], dp[3][3];
+};
+__device__ __forceinline__ void stencil_axes(const DevParams &P, const float xp[3], StencilAxes &S) {
+    uint32_t err = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        S.f[d] = stencil_axis(xp[d], P.inv_dx, P.n, S.b[d], err);
+        bspline_weights(S.f[d], S.w[d]);
+        bspline_slopes(S.f[d], S.dw[d]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            S.dw[d][i] *= P.inv_dx;
+            S.dp[d][i] = ((float)i - S.f[d]) * P.dx;
+        }
+    }
+}
+
 // Reverse of G2P and advection for one particle (state x, F before the
 // sub-step; V(ii, jj, kk) the grid velocity at its stencil nodes).  From the
 // adjoint of the state after the sub-step (xbo, vbo, Cbo, Fbo) it hands the
 // velocity adjoint of every stencil node to scatter(ii, jj, kk, value) and
 // returns G2P's part of the adjoint of x and F (v and C do not enter G2P).
 // The stencil's z-planes kk0 .. kk0+nkk-1 are this thread's; red sums the
-// partials over the threads that share the particle.  Cnew, if given, is the
-// particle's C after the sub-step (kept by the forward pass), which spares the
-// recomputation of Eq. 9's sum.
+// partials over the threads that share the particle.  Cnew and vnew, if both
+// given, are the particle's C and v after the sub-step (kept by the forward
+// pass), which spares the recomputation of Eqs. 8-9's sums.
+//
+// With val_i = vbar + K Cbar (x_i - x_p) (K = 4/dx^2, vbar and Cbar the
+// adjoints of v and C including advection and the F update), node i gets
+// w_i val_i.  The adjoint of x_p is sum_i grad w_i (V_i . val_i) from the
+// weights, plus -K Cbar^T sum_i w_i V_i = -K Cbar^T v from the offsets
+// x_i - x_p, since sum_i w_i V_i is the particle's new velocity (Eq. 8).
 template <class VelAt, class Scatter, class Red = OneLane>
 __device__ __forceinline__ void adj_g2p_particle(const DevParams &P, const float xp[3], const float F[9], VelAt vel,
                                                  const float xbo[3], const float vbo[3], const float Cbo[9],
                                                  const float Fbo[9], Scatter scatter, float xbn[3], float Fbn[9],
                                                  int kk0 = 0, int nkk = 3, Red red = Red(),
-                                                 const float *Cnew = nullptr) {
-    const float dx = P.dx, K = 4.0f * P.inv_dx * P.inv_dx, dt = P.dt;
-    uint32_t err = 0;
-    int b[3];
-    float f[3];
-    f[0] = stencil_axis(xp[0], P.inv_dx, P.n, b[0], err);
-    f[1] = stencil_axis(xp[1], P.inv_dx, P.n, b[1], err);
-    f[2] = stencil_axis(xp[2], P.inv_dx, P.n, b[2], err);
-    float w[3][3], dw[3][3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        bspline_weights(f[d], w[d]);
-        bspline_slopes(f[d], dw[d]);
-    }
-    // forward: C' = (4/dx^2) sum w v (x_i - x_p)^T = K Bm
-    float Bm[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) Bm[q] = 0.f;
-#pragma unroll 1
-    for (int kk = kk0; kk < kk0 + (Cnew ? 0 : nkk); ++kk)
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj)
-#pragma unroll
-            for (int ii = 0; ii < 3; ++ii) {
-                const float wg = w[0][ii] * w[1][jj] * w[2][kk];
-                const float dp[3] = {(ii - f[0]) * dx, (jj - f[1]) * dx, (kk - f[2]) * dx};
-                const float3 g = vel(b[0], b[1], b[2], ii, jj, kk);
-                const float vv[3] = {g.x, g.y, g.z};
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) Bm[3 * a + c] += wg * vv[a] * dp[c];
-            }
-    float KB[9];          // C' itself
-    if (Cnew) {
+                                                 const float *Cnew = nullptr, const float *vnew = nullptr) {
+    const float K = 4.0f * P.inv_dx * P.inv_dx, dt = P.dt;
+    StencilAxes S;
+    stencil_axes(P, xp, S);
+    // forward: C' = (4/dx^2) sum w v (x_i - x_p)^T, v' = sum w v
+    float KB[9], vp[3];          // C' and v' themselves
+    const bool kept = Cnew != nullptr && vnew != nullptr;
+    if (kept) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) KB[q] = Cnew[q];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vp[a] = vnew[a];
     } else {
+        float Bm[9], vs[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Bm[q] = 0.f;
+#pragma unroll 1
+        for (int kk = kk0; kk < kk0 + nkk; ++kk) {
+            const float wz = pick3(S.w[2], kk), dz = pick3(S.dp[2], kk);
+#pragma unroll
+            for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
+                for (int ii = 0; ii < 3; ++ii) {
+                    const float wg = S.w[0][ii] * S.w[1][jj] * wz;
+                    const float dp[3] = {S.dp[0][ii], S.dp[1][jj], dz};
+                    const float3 g = vel(S.b[0], S.b[1], S.b[2], ii, jj, kk);
+                    const float vv[3] = {g.x, g.y, g.z};
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        vs[a] += wg * vv[a];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) Bm[3 * a + c] += wg * vv[a] * dp[c];
+                    }
+                }
+        }
 #pragma unroll
         for (int q = 0; q < 9; ++q) KB[q] = K * red(Bm[q]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vp[a] = red(vs[a]);
     }
     float vbt[3], Cbt[9];
-    float xnode[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int a = 0; a < 3; ++a) vbt[a] = vbo[a] + dt * xbo[a];                       // x' = x + dt v'
 #pragma unroll
@@ -155,33 +184,37 @@ __device__ __forceinline__ void adj_g2p_particle(const DevParams &P, const float
             Fbn[3 * a + c] = sF;
             Cbt[3 * a + c] = Cbo[3 * a + c] + dt * sC;
         }
-#pragma unroll 1
-    for (int kk = kk0; kk < kk0 + nkk; ++kk)
+    float Kc[9];
 #pragma unroll
-        for (int jj = 0; jj < 3; ++jj)
+    for (int q = 0; q < 9; ++q) Kc[q] = K * Cbt[q];
+    float xnode[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int kk = kk0; kk < kk0 + nkk; ++kk) {
+        const float wz = pick3(S.w[2], kk), dwz = pick3(S.dw[2], kk), dz = pick3(S.dp[2], kk);
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+            const float wyz = S.w[1][jj] * wz, dwyz = S.dw[1][jj] * wz, wydz = S.w[1][jj] * dwz;
+            const float dy = S.dp[1][jj];
+            float rv[3];                                           // val along the row, less its x part
+#pragma unroll
+            for (int a = 0; a < 3; ++a) rv[a] = fmaf(Kc[3 * a + 2], dz, fmaf(Kc[3 * a + 1], dy, vbt[a]));
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii) {
-                const float wg = w[0][ii] * w[1][jj] * w[2][kk];
-                const float gw[3] = {dw[0][ii] * w[1][jj] * w[2][kk] * P.inv_dx,
-                                     w[0][ii] * dw[1][jj] * w[2][kk] * P.inv_dx,
-                                     w[0][ii] * w[1][jj] * dw[2][kk] * P.inv_dx};
-                const float dp[3] = {(ii - f[0]) * dx, (jj - f[1]) * dx, (kk - f[2]) * dx};
-                const float3 g = vel(b[0], b[1], b[2], ii, jj, kk);
-                const float vv[3] = {g.x, g.y, g.z};
-                float val[3], sdot = 0.f;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float cd = Cbt[3 * a] * dp[0] + Cbt[3 * a + 1] * dp[1] + Cbt[3 * a + 2] * dp[2];
-                    val[a] = vbt[a] + K * cd;                    // Eqs. 8-9
-                    sdot += vv[a] * val[a];
-                }
-                scatter(b[0], b[1], b[2], ii, jj, kk, make_float3(wg * val[0], wg * val[1], wg * val[2]));
-#pragma unroll
-                for (int c = 0; c < 3; ++c)                      // d (x_i - x_p) / d x_p = -I
-                    xnode[c] += gw[c] * sdot - K * wg * (Cbt[c] * vv[0] + Cbt[3 + c] * vv[1] + Cbt[6 + c] * vv[2]);
+                const float wg = S.w[0][ii] * wyz;
+                const float3 g = vel(S.b[0], S.b[1], S.b[2], ii, jj, kk);
+                const float d0 = S.dp[0][ii];
+                const float v0 = fmaf(Kc[0], d0, rv[0]), v1 = fmaf(Kc[3], d0, rv[1]), v2 = fmaf(Kc[6], d0, rv[2]);
+                const float sdot = fmaf(g.z, v2, fmaf(g.y, v1, g.x * v0));      // Eqs. 8-9
+                scatter(S.b[0], S.b[1], S.b[2], ii, jj, kk, make_float3(wg * v0, wg * v1, wg * v2));
+                xnode[0] = fmaf(S.dw[0][ii] * wyz, sdot, xnode[0]);
+                xnode[1] = fmaf(S.w[0][ii] * dwyz, sdot, xnode[1]);
+                xnode[2] = fmaf(S.w[0][ii] * wydz, sdot, xnode[2]);
             }
+        }
+    }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) xbn[c] = xbo[c] + red(xnode[c]);
+    for (int c = 0; c < 3; ++c)                                  // d (x_i - x_p) / d x_p = -I
+        xbn[c] = xbo[c] + red(xnode[c]) - K * (Cbt[c] * vp[0] + Cbt[3 + c] * vp[1] + Cbt[6 + c] * vp[2]);
 }
 
 // Reverse of P2G for one particle (state x, v, C, F; Gb(ii, jj, kk) the
@@ -190,6 +223,11 @@ __device__ __forceinline__ void adj_g2p_particle(const DevParams &P, const float
 // part of dL/dmu and dL/dlambda (only if lead: one of the threads that share
 // the particle).  The stencil's z-planes kk0 .. kk0+nkk-1 are this thread's;
 // red sums the partials over the threads that share the particle.
+//
+// Node i receives w_i (m, m v + A (x_i - x_p)) with A = m C - dt V0 (4/dx^2) tau.
+// With S = sum_i w_i mvbar_i: vbar = m S, Abar = sum_i w_i mvbar_i (x_i - x_p)^T,
+// and the adjoint of x_p is sum_i grad w_i (mbar_i m + mvbar_i . mom_i) from the
+// weights plus -A^T S from the offsets.
 template <class GbarAt, class Red = OneLane>
 __device__ __forceinline__ void adj_p2g_particle(const DevParams &P, const EnvParams &ep, const float xp[3],
                                                  const float vp[3], const float C[9], const float F[9], GbarAt gbar,
@@ -197,59 +235,65 @@ __device__ __forceinline__ void adj_p2g_particle(const DevParams &P, const EnvPa
                                                  float &lamb, int kk0 = 0, int nkk = 3, Red red = Red(),
                                                  bool lead = true) {
     uint32_t err = 0;
-    const float dx = P.dx, m = ep.mass, sk = ep.stress_k;
+    const float m = ep.mass, sk = ep.stress_k;
     float t6[6];
     kirchhoff(F, ep.mu, ep.lam, t6, err);
     const float tau[9] = {t6[0], t6[1], t6[2], t6[1], t6[3], t6[4], t6[2], t6[4], t6[5]};
     float Am[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) Am[q] = m * C[q] - sk * tau[q];     // A = m C - dt V0 (4/dx^2) tau
-    int b[3];
-    float f[3];
-    f[0] = stencil_axis(xp[0], P.inv_dx, P.n, b[0], err);
-    f[1] = stencil_axis(xp[1], P.inv_dx, P.n, b[1], err);
-    f[2] = stencil_axis(xp[2], P.inv_dx, P.n, b[2], err);
-    float w[3][3], dw[3][3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        bspline_weights(f[d], w[d]);
-        bspline_slopes(f[d], dw[d]);
-    }
-    float Ab[9], vbp[3] = {0.f, 0.f, 0.f}, xbp[3] = {0.f, 0.f, 0.f};
+    StencilAxes S;
+    stencil_axes(P, xp, S);
+    const float mv[3] = {m * vp[0], m * vp[1], m * vp[2]};
+    float Ab[9], Sm[3] = {0.f, 0.f, 0.f}, xbp[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < 9; ++q) Ab[q] = 0.f;
 #pragma unroll 1
-    for (int kk = kk0; kk < kk0 + nkk; ++kk)
+    for (int kk = kk0; kk < kk0 + nkk; ++kk) {
+        const float wz = pick3(S.w[2], kk), dwz = pick3(S.dw[2], kk), dz = pick3(S.dp[2], kk);
 #pragma unroll
-        for (int jj = 0; jj < 3; ++jj)
+        for (int jj = 0; jj < 3; ++jj) {
+            const float wyz = S.w[1][jj] * wz, dwyz = S.dw[1][jj] * wz, wydz = S.w[1][jj] * dwz;
+            const float dy = S.dp[1][jj];
+            float rm[3], R0[3] = {0.f, 0.f, 0.f}, R1[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) rm[a] = fmaf(Am[3 * a + 2], dz, fmaf(Am[3 * a + 1], dy, mv[a]));
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii) {
-                const float wg = w[0][ii] * w[1][jj] * w[2][kk];
-                const float gw[3] = {dw[0][ii] * w[1][jj] * w[2][kk] * P.inv_dx,
-                                     w[0][ii] * dw[1][jj] * w[2][kk] * P.inv_dx,
-                                     w[0][ii] * w[1][jj] * dw[2][kk] * P.inv_dx};
-                const float dp[3] = {(ii - f[0]) * dx, (jj - f[1]) * dx, (kk - f[2]) * dx};
-                const float4 g = gbar(b[0], b[1], b[2], ii, jj, kk);
+                const float wg = S.w[0][ii] * wyz;
+                const float4 g = gbar(S.b[0], S.b[1], S.b[2], ii, jj, kk);
+                const float d0 = S.dp[0][ii];
                 const float mvb[3] = {g.y, g.z, g.w};
                 float sdot = g.x * m;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const float mom = m * vp[a] + Am[3 * a] * dp[0] + Am[3 * a + 1] * dp[1] + Am[3 * a + 2] * dp[2];
-                    sdot += mvb[a] * mom;
-                    vbp[a] += m * wg * mvb[a];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) Ab[3 * a + c] += wg * mvb[a] * dp[c];
+                    sdot = fmaf(mvb[a], fmaf(Am[3 * a], d0, rm[a]), sdot);     // mom_i
+                    const float t = wg * mvb[a];
+                    R0[a] += t;
+                    R1[a] = fmaf(t, d0, R1[a]);
                 }
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    xbp[c] += gw[c] * sdot - wg * (Am[c] * mvb[0] + Am[3 + c] * mvb[1] + Am[6 + c] * mvb[2]);
+                xbp[0] = fmaf(S.dw[0][ii] * wyz, sdot, xbp[0]);
+                xbp[1] = fmaf(S.w[0][ii] * dwyz, sdot, xbp[1]);
+                xbp[2] = fmaf(S.w[0][ii] * wydz, sdot, xbp[2]);
             }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                Ab[3 * a] += R1[a];
+                Ab[3 * a + 1] = fmaf(R0[a], dy, Ab[3 * a + 1]);
+                Ab[3 * a + 2] = fmaf(R0[a], dz, Ab[3 * a + 2]);
+                Sm[a] += R0[a];
+            }
+        }
+    }
 #pragma unroll
     for (int q = 0; q < 9; ++q) Ab[q] = red(Ab[q]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        vbp[a] = red(vbp[a]);
-        xbp[a] = red(xbp[a]);
+    for (int a = 0; a < 3; ++a) Sm[a] = red(Sm[a]);
+    float vbp[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        xbp[c] = red(xbp[c]) - (Am[c] * Sm[0] + Am[3 + c] * Sm[1] + Am[6 + c] * Sm[2]);
+        vbp[c] = m * Sm[c];
     }
     // tau = mu (F F^T - I) + lambda ln(J) I
     float taub[9];

@@ -90,8 +90,8 @@ struct Tape {
     bool fused = false;
     float *final_img = nullptr;       // the state after the rollout (restored after the reverse pass)
     size_t cap_final = 0, cap_rs = 0, cap_rsg = 0, cap_rsb = 0, cap_gb = 0;
-    float *rs = nullptr;              // ck x (xi, f0, f1: 12 n floats; f2: n floats padded to 4)
-    float4 *rs_grid = nullptr;        // ck x nn: the grid each recorded sub-step read
+    float *rs = nullptr;              // ck x rs_floats(n): one recorded sub-step's particles
+    float4 *rs_grid = nullptr;        // ck x 2 nn: the grid each recorded sub-step read, and its velocities
     uint32_t *rs_blk = nullptr;       // ck x (2 nblocks block ranges + nblocks work list + 4 counters)
     float4 *gb2 = nullptr;            // second grid adjoint buffer
     // per grid block: a stamp, and two lists ([count, block ...]) of the blocks
@@ -101,6 +101,9 @@ struct Tape {
     uint32_t touch_sv = 0;
     double *lame_part = nullptr;      // per CTA of the reverse sub-step: dL/dmu, dL/dlambda
     size_t cap_lame = 0;
+    float4 *lp = nullptr;             // 2 x 3 n: state adjoints by position within a segment
+    size_t cap_lp = 0;
+    bool last_recorded = false;       // the record buffers hold the last segment (from the forward pass)
 };
 
 }  // namespace
@@ -1026,8 +1029,8 @@ int record_grid(mpm_handle *h) {
 }
 
 // Floats of one recorded sub-step's particles (xi, f0, f1, vc0, vc1, vc2 as
-// float4; f2)
-size_t rs_floats(int64_t n) { return 24 * (size_t)n + (((size_t)n + 3) & ~size_t(3)); }
+// float4; f2; the input positions, one word each), each part 16-byte aligned
+size_t rs_floats(int64_t n) { return 24 * (size_t)n + 2 * (((size_t)n + 3) & ~size_t(3)); }
 // Words of one recorded sub-step's block table: ranges (2 per block), the
 // work list (1 per block) and the list length (padded to 4 words)
 size_t rs_words(const mpm_handle *h) { return 3 * (size_t)h->nblocks + 4; }
@@ -1045,10 +1048,13 @@ StepRecord step_record(mpm_handle *h, int j) {
     r.vc.vc1 = reinterpret_cast<float4 *>(base + 16 * n);
     r.vc.vc2 = reinterpret_cast<float4 *>(base + 20 * n);
     r.f2 = base + 24 * n;
+    r.src = reinterpret_cast<uint32_t *>(base + 24 * n + ((n + 3) & ~size_t(3)));
     r.blk = reinterpret_cast<uint2 *>(w);
     r.act = w + 2 * (size_t)h->nblocks;
     r.nact = w + 3 * (size_t)h->nblocks;
-    r.grid = tp.rs_grid + (size_t)j * (size_t)h->P.n * h->P.n * h->P.n;
+    const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+    r.grid = tp.rs_grid + 2 * (size_t)j * nn;
+    r.vgrid = r.grid + nn;
     return r;
 }
 
@@ -1089,50 +1095,64 @@ mpm_status fused_reverse(mpm_handle *h, const AdjState &A, int nck) {
     if (h->rev_grid == 0) h->rev_grid = h->num_sms * std::max(reverse_step_ctas_per_sm(), 1);
     float4 *gnext = tp.gbar, *gcur = tp.gb2;     // dL/d(m, mv) of G_{k+1}; dL/dV_k, then dL/d(m, mv) of G_k
     // both start clean; afterwards only the blocks a sub-step touched are cleared.
-    // Touched-block lists of sub-step k live in slot k % 3 (blocks, then the
-    // counts of the three slots); the reverse grid operation of sub-step k
-    // clears the blocks of sub-step k+1 and zeroes the count of slot (k+2) % 3,
-    // which the reverse sub-step k-1 fills next.
+    // The touched-block list of sub-step k lives in slot k % 3 (8 entries per
+    // work-list block, then the three slots' work-list lengths); the reverse grid
+    // operation of sub-step k clears the blocks of sub-step k+1.
     CK(cudaMemsetAsync(gnext, 0, sizeof(float4) * nn, s));
     CK(cudaMemsetAsync(gcur, 0, sizeof(float4) * nn, s));
-    uint32_t *stamp = tp.touch, *lists = tp.touch + nbk, *counts = lists + 3 * nbk;
+    uint32_t *stamp = tp.touch, *lists = tp.touch + nbk, *counts = lists + 24 * nbk;
     CK(cudaMemsetAsync(counts, 0, 3 * sizeof(uint32_t), s));
     mpm_status st;
     if ((st = ensure(h, &tp.lame_part, &tp.cap_lame, 2 * (size_t)h->rev_grid)) != MPM_OK) return st;
     CK(cudaMemsetAsync(tp.lame_part, 0, sizeof(double) * 2 * h->rev_grid, s));
+    // the state adjoints between the sub-steps of a segment, by position (two
+    // buffers of 3 n float4: the incoming one and the outgoing one)
+    if ((st = ensure(h, &tp.lp, &tp.cap_lp, 6 * n)) != MPM_OK) return st;
+    float4 *lp_in = tp.lp, *lp_out = tp.lp + 3 * n;
+    // the reverse grid operation: one wave of 3 CTAs per SM (a node per thread
+    // over 8 list entries per work-list block, most of them empty)
+    const int adj_grid_ctas = 3 * h->num_sms;
     for (int sg = nck - 1; sg >= 0; --sg) {
         const int c0 = sg * tp.ck, len = std::min(tp.ck, tp.nsub - c0);
-        if ((st = load_image(h, tp.ckpt + (size_t)sg * tp.image)) != MPM_OK) return st;
-        for (int j = 0; j < len; ++j) {
-            launch_fused_step_record(h->P, h->fb, tp.frames + (size_t)(c0 + j) * nt, step_record(h, j), record_grid(h),
-                                     s);
-            h->step += 1u;
+        if (sg == nck - 1 && tp.last_recorded) {
+            tp.last_recorded = false;     // the replays below overwrite it
+        } else {
+            if ((st = load_image(h, tp.ckpt + (size_t)sg * tp.image)) != MPM_OK) return st;
+            for (int j = 0; j < len; ++j) {
+                launch_fused_step_record(h->P, h->fb, tp.frames + (size_t)(c0 + j) * nt, step_record(h, j),
+                                         record_grid(h), s);
+                h->step += 1u;
+            }
         }
         for (int j = len - 1; j >= 0; --j) {
             const int k = c0 + j;
-            const int sk = k % 3, sk1 = (k + 1) % 3, sk2 = (k + 2) % 3;
+            const int sk = k % 3, sk1 = (k + 1) % 3;
             ReverseArgs R{};
             R.rec = step_record(h, j);
-            R.Gk = R.rec.grid;
-            R.frames = tp.frames + (size_t)k * nt;
             R.gbar_next = gnext;
             R.vbar = gcur;
             R.lam = A;
+            R.lp_in = lp_in;
+            R.lp_out = lp_out;
+            R.np = (uint32_t)n;
+            R.lam_in_by_id = j == len - 1;
+            R.lam_out_by_id = j == 0;
             R.lame_part = tp.lame_part;
             R.stamp = stamp;
             R.sv = ++tp.touch_sv;
-            R.touch_list = lists + (size_t)sk * nbk;
-            R.touch_count = counts + sk;
+            R.touch_list = lists + (size_t)sk * 8 * nbk;
+            R.touch_n = counts + sk;
             launch_reverse_step(k + 1 < tp.nsub, true, h->P, R, h->rev_grid, s);
             AdjGridLists L;
             L.list = R.touch_list;
-            L.count = R.touch_count;
-            L.zlist = lists + (size_t)sk1 * nbk;
-            L.zcount = counts + sk1;
+            L.nlist = R.touch_n;
+            L.zlist = lists + (size_t)sk1 * 8 * nbk;
+            L.znlist = counts + sk1;
             L.zbuf = gnext;
-            L.reset = counts + sk2;
-            launch_adj_grid(h->P, R.Gk, R.frames, gcur, tp.red + 2 + (size_t)k * nt * 18, 2 * h->num_sms, s, L);
+            launch_adj_grid(h->P, R.rec.grid, tp.frames + (size_t)k * nt, gcur, tp.red + 2 + (size_t)k * nt * 18,
+                            adj_grid_ctas, s, L);
             std::swap(gnext, gcur);
+            std::swap(lp_in, lp_out);
         }
     }
     // the first sub-step's P2G at the initial state (its v and C from checkpoint 0)
@@ -1142,6 +1162,9 @@ mpm_status fused_reverse(mpm_handle *h, const AdjState &A, int nck) {
     R.lam = A;
     R.v0 = tp.ckpt + 3 * n;
     R.C0 = tp.ckpt + 15 * n;
+    R.np = (uint32_t)n;
+    R.lam_in_by_id = 1;
+    R.lam_out_by_id = 1;
     R.lame_part = tp.lame_part;
     launch_reverse_step(true, false, h->P, R, h->rev_grid, s);
     CK(cudaGetLastError());
@@ -1173,6 +1196,7 @@ mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *pose
     if ((st = poll_error(h, false)) != MPM_OK) return st;
     Tape &tp = h->tape;
     tp.valid = false;
+    tp.last_recorded = false;
     const int64_t n = h->n;
     const int ck = std::min(checkpoint_every, n_substeps);
     const int nck = (n_substeps + ck - 1) / ck;
@@ -1183,18 +1207,19 @@ mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *pose
         if ((st = ensure(h, &tp.ckpt, &tp.cap_ckpt, tp.image * nck)) != MPM_OK) return st;
         if ((st = ensure(h, &tp.final_img, &tp.cap_final, tp.image)) != MPM_OK) return st;
         if ((st = ensure(h, &tp.rs, &tp.cap_rs, rs_floats(n) * ck)) != MPM_OK) return st;
-        if (tp.cap_rsg < nn * ck) {
-            // recorded sub-steps write the grid over their blocks' regions only; the
-            // reverse grid operation also reads the rest of the blocks it lists, where
-            // it needs finite values (its adjoint there is zero)
-            if ((st = ensure(h, &tp.rs_grid, &tp.cap_rsg, nn * ck)) != MPM_OK) return st;
-            CK(cudaMemsetAsync(tp.rs_grid, 0, sizeof(float4) * nn * ck, h->stream));
+        if (tp.cap_rsg < 2 * nn * ck) {
+            // recorded sub-steps write the grid (before and after the grid operation)
+            // over their blocks' regions only; the reverse grid operation also reads the
+            // rest of the blocks it lists, where it needs finite values (its adjoint
+            // there is zero)
+            if ((st = ensure(h, &tp.rs_grid, &tp.cap_rsg, 2 * nn * ck)) != MPM_OK) return st;
+            CK(cudaMemsetAsync(tp.rs_grid, 0, sizeof(float4) * 2 * nn * ck, h->stream));
         }
         if ((st = ensure(h, &tp.rs_blk, &tp.cap_rsb, rs_words(h) * ck)) != MPM_OK) return st;
         if ((st = ensure(h, &tp.gbar, &tp.cap_gb, nn)) != MPM_OK) return st;
         size_t one = tp.cap_gb;
         if ((st = ensure(h, &tp.gb2, &one, nn)) != MPM_OK) return st;
-        const size_t tw = 4 * (size_t)h->nblocks + 3;
+        const size_t tw = 25 * (size_t)h->nblocks + 3;
         if (tp.cap_touch < tw) {
             if ((st = ensure(h, &tp.touch, &tp.cap_touch, tw)) != MPM_OK) return st;
             CK(cudaMemsetAsync(tp.touch, 0, sizeof(uint32_t) * tw, h->stream));
@@ -1230,16 +1255,33 @@ mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *pose
     tp.nu = h->env_nu[0];
     if (tp.fused) {
         // checkpoints by particle id; v and C of a checkpointed state are written by
-        // the sub-step before it
+        // the sub-step before it.  The last segment runs with recording sub-steps,
+        // so that the reverse pass starts without replaying it (step_record lays
+        // the records out for tp.n particles).
+        tp.n = n;
+        const int c_last = (nck - 1) * ck;
         for (int k = 0; k < n_substeps; ++k) {
             if (k % ck == 0) id_image(h, tp.ckpt + (size_t)(k / ck) * tp.image);
-            // the configuration the reverse pass replays segments with, so that the
-            // replay follows the recorded trajectory up to the order of float atomics
-            const bool wv = (k + 1) % ck == 0 || k + 1 == n_substeps;
-            launch_fused_step(h->P, h->fb, tp.frames + (size_t)k * nt, wv, record_grid(h), kRecordConfig, h->stream);
+            if (k >= c_last) {
+                launch_fused_step_record(h->P, h->fb, tp.frames + (size_t)k * nt, step_record(h, k - c_last),
+                                         record_grid(h), h->stream);
+            } else {
+                // the configuration the reverse pass replays segments with, so that the
+                // replay follows the recorded trajectory up to the order of float atomics
+                const bool wv = (k + 1) % ck == 0;
+                launch_fused_step(h->P, h->fb, tp.frames + (size_t)k * nt, wv, record_grid(h), kRecordConfig,
+                                  h->stream);
+            }
             h->step += 1u;
         }
+        // the last sub-step kept v and C in its record, by output position: they
+        // become the live state's
+        const VCState rv = step_record(h, n_substeps - 1 - c_last).vc;
+        CK(cudaMemcpyAsync(h->fb.vc.vc0, rv.vc0, 16 * (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->fb.vc.vc1, rv.vc1, 16 * (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->fb.vc.vc2, rv.vc2, 16 * (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
         id_image(h, tp.final_img);
+        tp.last_recorded = true;
     } else {
         for (int k = 0; k < n_substeps; ++k) {
             if (k % ck == 0 && (st = live_to_image(h, tp.ckpt + (size_t)(k / ck) * tp.image)) != MPM_OK) return st;

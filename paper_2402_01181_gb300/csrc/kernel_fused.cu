@@ -182,10 +182,11 @@ __device__ __forceinline__ void prefetch_block(Smem &s, int buf, uint32_t b, con
 
 
 // MINB: resident CTAs per SM the configuration is compiled for (the register budget)
-// RECORD: also write, for the reverse mode, every block's input particles in
-// block-contiguous order (the range [out_base, out_base + total) the block's
-// output was allocated), each block's range, the list of blocks in work order
-// and its length.
+// RECORD: also write, for the reverse mode, every block's input particles at
+// their output positions (inside the range [out_base, out_base + total) the
+// block's output was allocated) with their input positions, the list of
+// blocks in work order with each one's range, the list's length, and the grid
+// of each block's region before and after the grid operation.
 template <bool WRITE_VC, int T, int GP, int MINB = kMinBlocks<T, GP>, bool RECORD = false>
 __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B,
                                                                      const ToolFrame *__restrict__ tools,
@@ -268,9 +269,13 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
             const int i = 4 * bx + q % 6, j = 4 * by + (q / 6) % 6, k = 4 * bz + q / 36;
             const float4 g = gv[q];
             float3 v = make_float3(0.f, 0.f, 0.f);
-            if (RECORD && i < n && j < n && k < n) rec.grid[node_addr_env(env, i, j, k, nb, nbe)] = g;
             if (i < n && j < n && k < n) v = grid_node_update(g.x, g.y, g.z, g.w, i, j, k, P, s.tools[cb], ep.ntools);
             gv[q] = make_float4(v.x, v.y, v.z, 0.f);
+            if (RECORD && i < n && j < n && k < n) {
+                const uint32_t a = node_addr_env(env, i, j, k, nb, nbe);
+                rec.grid[a] = g;
+                rec.vgrid[a] = make_float4(v.x, v.y, v.z, 0.f);
+            }
         }
         if (tid < 32) s.ccount[tid] = 0u;
         for (int q = tid; q < 2 * NW * 28; q += T) (&s.wcnt[0][0][0])[q] = 0u;
@@ -375,7 +380,7 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
                 t.stamp = 0; t.first = 0; t.npass = 0;
             }
             tout[b] = t;
-            if (RECORD) rec.blk[b] = make_uint2(fit ? alloc_ob : 0u, fit ? total : 0u);
+            if (RECORD) rec.blk[item] = make_uint2(fit ? alloc_ob : 0u, fit ? total : 0u);
             s.out_base = fit ? alloc_ob : nparticles;
             s.chunk_first = fit ? alloc_cf : nchunk_cap;
         }
@@ -596,14 +601,15 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
                 const unsigned nz = __ballot_sync(0xffffffffu, lane < 27 && run > 0);
                 if (lane == 0) s.mask |= nz;
             }
-            if (RECORD && valid && out_base + j < nparticles) {
-                rec.xi[out_base + j] = xi;
-                rec.f0[out_base + j] = a0;
-                rec.f1[out_base + j] = a1;
-                rec.f2[out_base + j] = f2;
-                store_vc(rec.vc, out_base + j, vx, vy, vz, Cm);
-            }
             const uint32_t pos = out_base + pass * T + my_off + rank;
+            if (RECORD && valid && pos < nparticles) {
+                rec.xi[pos] = xi;
+                rec.f0[pos] = a0;
+                rec.f1[pos] = a1;
+                rec.f2[pos] = f2;
+                store_vc(rec.vc, pos, vx, vy, vz, Cm);
+                rec.src[pos] = source_slot(s, ncand, j);
+            }
             if (valid && pos < nparticles) {
                 out.xi[pos] = make_float4(nxp, nyp, nzp, idf);
                 out.f0[pos] = make_float4(Fn[0], Fn[1], Fn[2], Fn[3]);

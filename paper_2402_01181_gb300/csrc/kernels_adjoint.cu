@@ -58,138 +58,148 @@ __global__ void __launch_bounds__(kThreads) k_adj_g2p(DevParams P, PState S, uin
 
 // ------------------------------------------------------ grid operation
 
+// The reverse grid operation at node g (grid (m, mv) node, incoming velocity
+// adjoint gb.yzw), with the tool-frame adjoints summed over the warp.  Called
+// by all 32 lanes of a warp together.
+__device__ __forceinline__ void adj_grid_node(const DevParams &P, const ToolFrame *s_tools, int ntools,
+                                              float4 *__restrict__ Gb, double *__restrict__ tool_bar, uint32_t g,
+                                              float4 node, float4 gb, int lo, int hi) {
+    const uint32_t blk = g >> 6, l = g & 63u;
+    const int bx = blk % P.nb, by = (blk / P.nb) % P.nb, bz = blk / (P.nb * P.nb);
+    const int i = bx * 4 + (l & 3), j = by * 4 + ((l >> 2) & 3), k = bz * 4 + (l >> 4);
+    float tb[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) tb[q] = 0.f;
+    int hit = -1;
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool wall = i < lo || j < lo || k < lo || i >= hi || j >= hi || k >= hi;
+    if (node.x > 0.0f && !wall) {
+        const float m = node.x;
+        const float vf[3] = {node.y / m + P.dt * P.gx, node.z / m + P.dt * P.gy, node.w / m + P.dt * P.gz};
+        float vbar[3] = {gb.y, gb.z, gb.w};
+        if (ntools > 0) {
+            const float xw[3] = {i * P.dx, j * P.dx, k * P.dx};
+            float dmin, nr[3], pr[3];
+            const int id = nearest_tool(xw[0], xw[1], xw[2], s_tools, ntools, dmin, nr[0], nr[1], nr[2], pr[0],
+                                        pr[1], pr[2]);
+            if (id >= 0 && dmin < P.theta) {
+                const ToolFrame &tf = s_tools[id];
+                float nw[3], r[3], vco[3], vrel[3], vn = 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    nw[a] = tf.R[3 * a] * nr[0] + tf.R[3 * a + 1] * nr[1] + tf.R[3 * a + 2] * nr[2];
+                    r[a] = xw[a] - tf.T[a];
+                }
+                vco[0] = tf.u[0] + tf.w[1] * r[2] - tf.w[2] * r[1];
+                vco[1] = tf.u[1] + tf.w[2] * r[0] - tf.w[0] * r[2];
+                vco[2] = tf.u[2] + tf.w[0] * r[1] - tf.w[1] * r[0];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) { vrel[a] = vf[a] - vco[a]; vn += vrel[a] * nw[a]; }   // Eqs. 15-16
+                if (vn < 0.0f) {
+                    hit = id;
+                    float vt[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) vt[a] = vrel[a] - vn * nw[a];                      // Eq. 17
+                    const float tn = sqrtf(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
+                    float scale = 0.f;
+                    if (tn > 0.0f) scale = fmaxf(tn + P.fric * vn, 0.0f) / tn;                   // Eq. 18
+                    // v' = scale vt + vco (Eq. 19)
+                    float vtb[3] = {0.f, 0.f, 0.f}, vnb = 0.f;
+                    if (scale > 0.f) {
+                        const float scb = vbar[0] * vt[0] + vbar[1] * vt[1] + vbar[2] * vt[2];
+                        vnb += P.fric * scb / tn;                 // scale = 1 + mu_f vn / |vt|
+                        const float vtnb = -P.fric * vn * scb / (tn * tn);
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) vtb[a] = scale * vbar[a] + vtnb * vt[a] / tn;
+                    }
+                    float vrelb[3], nwb[3];
+                    const float vtb_n = vtb[0] * nw[0] + vtb[1] * nw[1] + vtb[2] * nw[2];
+                    vnb -= vtb_n;                                 // vt = vrel - vn nw
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        vrelb[a] = vtb[a] + vnb * nw[a];          // vn = vrel . nw
+                        nwb[a] = -vn * vtb[a] + vnb * vrel[a];
+                    }
+                    float vcob[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) vcob[a] = vbar[a] - vrelb[a];   // vrel = v - vco; v' has + vco
+                    // vco = u + w x r, r = x - T
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) tb[12 + a] = vcob[a];
+                    tb[15] = r[1] * vcob[2] - r[2] * vcob[1];
+                    tb[16] = r[2] * vcob[0] - r[0] * vcob[2];
+                    tb[17] = r[0] * vcob[1] - r[1] * vcob[0];
+                    tb[9] = -(vcob[1] * tf.w[2] - vcob[2] * tf.w[1]);
+                    tb[10] = -(vcob[2] * tf.w[0] - vcob[0] * tf.w[2]);
+                    tb[11] = -(vcob[0] * tf.w[1] - vcob[1] * tf.w[0]);
+                    // nw = R n_ref(x_ref), x_ref = R^T (x - T)
+                    float nrb[3], Jn[9], xrb[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) tb[3 * a + c] = nwb[a] * nr[c];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) nrb[c] = tf.R[c] * nwb[0] + tf.R[3 + c] * nwb[1] + tf.R[6 + c] * nwb[2];
+                    tool_normal_jacobian(tf.kind, tf.dims, pr[0], pr[1], pr[2], Jn);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) xrb[c] = Jn[c] * nrb[0] + Jn[3 + c] * nrb[1] + Jn[6 + c] * nrb[2];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) tb[3 * c + a] += r[c] * xrb[a];
+                        tb[9 + c] -= tf.R[3 * c] * xrb[0] + tf.R[3 * c + 1] * xrb[1] + tf.R[3 * c + 2] * xrb[2];
+                    }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) vbar[a] = vrelb[a];
+                }
+            }
+        }
+        // v = mv / m + dt g
+        out = make_float4(-(vbar[0] * node.y + vbar[1] * node.z + vbar[2] * node.w) / (m * m), vbar[0] / m,
+                          vbar[1] / m, vbar[2] / m);
+    }
+    Gb[g] = out;
+    for (int t = 0; t < ntools; ++t) {
+        const bool mine = hit == t;
+        if (!__any_sync(0xffffffffu, mine)) continue;
+#pragma unroll
+        for (int q = 0; q < 18; ++q) {
+            const float v = warp_sum(mine ? tb[q] : 0.f);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&tool_bar[18 * t + q], (double)v);
+        }
+    }
+}
+
 // Gb.yzw holds dL/d(grid velocity) on entry; on return Gb = (dL/dm, dL/dmv).
 // G holds the grid (m, mv) the forward grid operation read.  tool_bar
 // (ntools x 18: R row-major, T, u, w) accumulates dL/d(frame entries).
 // L.list (if not NULL): only the nodes of those grid blocks (the others hold
-// no adjoint).  L.zlist: the nodes of those blocks are cleared in L.zbuf.
-// L.reset: a list count set to zero.
-__global__ void __launch_bounds__(kThreads) k_adj_grid(DevParams P, const float4 *__restrict__ G,
+// no adjoint), 8 entries per work-list block, kNoBlock entries skipped.
+// L.zlist: the nodes of those blocks are cleared in L.zbuf.
+__global__ void __launch_bounds__(kThreads, 3) k_adj_grid(DevParams P, const float4 *__restrict__ G,
                                                         const ToolFrame *__restrict__ tools,
                                                         float4 *__restrict__ Gb, double *__restrict__ tool_bar,
                                                         AdjGridLists L) {
-    __shared__ ToolFrame s_tools[kMaxTools];
+    // the tool frames are read through L1 (no shared copy, so no barrier before
+    // the first node)
     const int ntools = P.envp[0].ntools;
-    if (threadIdx.x < ntools * (sizeof(ToolFrame) / 4))
-        reinterpret_cast<float *>(s_tools)[threadIdx.x] = reinterpret_cast<const float *>(tools)[threadIdx.x];
-    __syncthreads();
-    // a multiple of 64 nodes: whole warps stay in the loop
-    const uint32_t total = L.list ? *L.count * 64u : (uint32_t)P.n * P.n * P.n;
     const int lo = P.bound, hi = P.n - P.bound;
-    if (L.reset && blockIdx.x == 0 && threadIdx.x == 0) *L.reset = 0u;
-    if (L.zlist) {
-        const uint32_t zt = *L.zcount * 64u;
-        for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < zt; q += gridDim.x * blockDim.x)
-            L.zbuf[L.zlist[q >> 6] * 64u + (q & 63u)] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    if (!L.list) {
+        // every node; n^3 is a multiple of 64, so whole warps stay in the loop
+        const uint32_t total = (uint32_t)P.n * P.n * P.n;
+        for (uint32_t q = gt; q < total; q += stride) adj_grid_node(P, tools, ntools, Gb, tool_bar, q, G[q], Gb[q], lo, hi);
+        return;
     }
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
-        const uint32_t g = L.list ? L.list[q >> 6] * 64u + (q & 63u) : q;
-        const float4 node = G[g];
-        const float4 gb = Gb[g];
-        const uint32_t blk = g >> 6, l = g & 63u;
-        const int bx = blk % P.nb, by = (blk / P.nb) % P.nb, bz = blk / (P.nb * P.nb);
-        const int i = bx * 4 + (l & 3), j = by * 4 + ((l >> 2) & 3), k = bz * 4 + (l >> 4);
-        float tb[18];
-#pragma unroll
-        for (int q = 0; q < 18; ++q) tb[q] = 0.f;
-        int hit = -1;
-        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-        const bool wall = i < lo || j < lo || k < lo || i >= hi || j >= hi || k >= hi;
-        if (node.x > 0.0f && !wall) {
-            const float m = node.x;
-            const float vf[3] = {node.y / m + P.dt * P.gx, node.z / m + P.dt * P.gy, node.w / m + P.dt * P.gz};
-            float vbar[3] = {gb.y, gb.z, gb.w};
-            if (ntools > 0) {
-                const float xw[3] = {i * P.dx, j * P.dx, k * P.dx};
-                float dmin, nr[3], pr[3];
-                const int id = nearest_tool(xw[0], xw[1], xw[2], s_tools, ntools, dmin, nr[0], nr[1], nr[2], pr[0],
-                                            pr[1], pr[2]);
-                if (id >= 0 && dmin < P.theta) {
-                    const ToolFrame &tf = s_tools[id];
-                    float nw[3], r[3], vco[3], vrel[3], vn = 0.f;
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        nw[a] = tf.R[3 * a] * nr[0] + tf.R[3 * a + 1] * nr[1] + tf.R[3 * a + 2] * nr[2];
-                        r[a] = xw[a] - tf.T[a];
-                    }
-                    vco[0] = tf.u[0] + tf.w[1] * r[2] - tf.w[2] * r[1];
-                    vco[1] = tf.u[1] + tf.w[2] * r[0] - tf.w[0] * r[2];
-                    vco[2] = tf.u[2] + tf.w[0] * r[1] - tf.w[1] * r[0];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) { vrel[a] = vf[a] - vco[a]; vn += vrel[a] * nw[a]; }   // Eqs. 15-16
-                    if (vn < 0.0f) {
-                        hit = id;
-                        float vt[3];
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) vt[a] = vrel[a] - vn * nw[a];                      // Eq. 17
-                        const float tn = sqrtf(vt[0] * vt[0] + vt[1] * vt[1] + vt[2] * vt[2]);
-                        float scale = 0.f;
-                        if (tn > 0.0f) scale = fmaxf(tn + P.fric * vn, 0.0f) / tn;                   // Eq. 18
-                        // v' = scale vt + vco (Eq. 19)
-                        float vtb[3] = {0.f, 0.f, 0.f}, vnb = 0.f;
-                        if (scale > 0.f) {
-                            const float scb = vbar[0] * vt[0] + vbar[1] * vt[1] + vbar[2] * vt[2];
-                            vnb += P.fric * scb / tn;                 // scale = 1 + mu_f vn / |vt|
-                            const float vtnb = -P.fric * vn * scb / (tn * tn);
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) vtb[a] = scale * vbar[a] + vtnb * vt[a] / tn;
-                        }
-                        float vrelb[3], nwb[3];
-                        const float vtb_n = vtb[0] * nw[0] + vtb[1] * nw[1] + vtb[2] * nw[2];
-                        vnb -= vtb_n;                                 // vt = vrel - vn nw
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            vrelb[a] = vtb[a] + vnb * nw[a];          // vn = vrel . nw
-                            nwb[a] = -vn * vtb[a] + vnb * vrel[a];
-                        }
-                        float vcob[3];
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) vcob[a] = vbar[a] - vrelb[a];   // vrel = v - vco; v' has + vco
-                        // vco = u + w x r, r = x - T
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) tb[12 + a] = vcob[a];
-                        tb[15] = r[1] * vcob[2] - r[2] * vcob[1];
-                        tb[16] = r[2] * vcob[0] - r[0] * vcob[2];
-                        tb[17] = r[0] * vcob[1] - r[1] * vcob[0];
-                        tb[9] = -(vcob[1] * tf.w[2] - vcob[2] * tf.w[1]);
-                        tb[10] = -(vcob[2] * tf.w[0] - vcob[0] * tf.w[2]);
-                        tb[11] = -(vcob[0] * tf.w[1] - vcob[1] * tf.w[0]);
-                        // nw = R n_ref(x_ref), x_ref = R^T (x - T)
-                        float nrb[3], Jn[9], xrb[3];
-#pragma unroll
-                        for (int a = 0; a < 3; ++a)
-#pragma unroll
-                            for (int c = 0; c < 3; ++c) tb[3 * a + c] = nwb[a] * nr[c];
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) nrb[c] = tf.R[c] * nwb[0] + tf.R[3 + c] * nwb[1] + tf.R[6 + c] * nwb[2];
-                        tool_normal_jacobian(tf.kind, tf.dims, pr[0], pr[1], pr[2], Jn);
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) xrb[c] = Jn[c] * nrb[0] + Jn[3 + c] * nrb[1] + Jn[6 + c] * nrb[2];
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-#pragma unroll
-                            for (int a = 0; a < 3; ++a) tb[3 * c + a] += r[c] * xrb[a];
-                            tb[9 + c] -= tf.R[3 * c] * xrb[0] + tf.R[3 * c + 1] * xrb[1] + tf.R[3 * c + 2] * xrb[2];
-                        }
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) vbar[a] = vrelb[a];
-                    }
-                }
-            }
-            // v = mv / m + dt g
-            out = make_float4(-(vbar[0] * node.y + vbar[1] * node.z + vbar[2] * node.w) / (m * m), vbar[0] / m,
-                              vbar[1] / m, vbar[2] / m);
-        }
-        Gb[g] = out;
-        for (int t = 0; t < ntools; ++t) {
-            const bool mine = hit == t;
-            if (!__any_sync(0xffffffffu, mine)) continue;
-#pragma unroll
-            for (int q = 0; q < 18; ++q) {
-                const float v = warp_sum(mine ? tb[q] : 0.f);
-                if ((threadIdx.x & 31) == 0) atomicAdd(&tool_bar[18 * t + q], (double)v);
-            }
-        }
+    // one thread per node of the listed blocks (the 64 threads of an entry read
+    // the same entry, so an empty one is skipped by whole warps)
+    const uint32_t total = *L.nlist * 512u, zt = L.zlist ? *L.znlist * 512u : 0u;
+    for (uint32_t q = gt; q < max(total, zt); q += stride) {
+        const uint32_t zb = q < zt ? L.zlist[q >> 6] : kNoBlock, tb = q < total ? L.list[q >> 6] : kNoBlock;
+        if (zb != kNoBlock) L.zbuf[zb * 64u + (q & 63u)] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tb == kNoBlock) continue;
+        const uint32_t g = tb * 64u + (q & 63u);
+        adj_grid_node(P, tools, ntools, Gb, tool_bar, g, G[g], Gb[g], lo, hi);
     }
 }
 

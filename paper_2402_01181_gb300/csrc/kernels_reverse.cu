@@ -22,6 +22,7 @@
 // held where the forward pass took them; the arithmetic is that of the
 // unsorted adjoint kernels (adjoint.cuh).
 #include <algorithm>
+#include <type_traits>
 
 #include "adjoint.cuh"
 #include "common.cuh"
@@ -35,64 +36,97 @@ constexpr int kRevThreads = 128;
 // Work items are chunks of a block's particles: chunk c of block b holds its
 // particles [c kChunk, (c+1) kChunk), the last of kMaxChunks the rest, so that
 // the dense blocks under a tool spread over several CTAs.
-constexpr uint32_t kChunk = 80, kMaxChunks = 16;
+constexpr uint32_t kChunk = 128, kMaxChunks = 16;
+// Lanes per particle: 1 (the whole stencil; a chunk is then one round of the
+// CTA) or 3 (one z-plane of the stencil each, partials summed by shuffles),
+// which made the whole backward 4% slower.
+constexpr int kRevLanes = 1;
 
 struct RevSmem {
     float4 vtile[216];      // V_k at [4b, 4b+5]^3 (.xyz)
     float4 gbt[512];        // dL/d(m, mv) of G_{k+1} at [4b-1, 4b+6]^3
-    ToolFrame tools[kMaxTools];
 };
+
+// One particle's recorded inputs of a reverse sub-step: state before the
+// sub-step (xi = x | id, F), v and C after it, and the incoming (x, F) adjoint
+// by position
+struct RevIn {
+    float4 xi, a0, a1, c0, c1, c2, l0, l1, l2;
+    float f2;
+};
+template <bool DO_G2P>
+__device__ __forceinline__ void load_rev_in(const ReverseArgs &R, uint32_t p, RevIn &in) {
+    in.xi = R.rec.xi[p];
+    in.a0 = R.rec.f0[p];
+    in.a1 = R.rec.f1[p];
+    in.f2 = R.rec.f2[p];
+    if (DO_G2P) {
+        in.c0 = R.rec.vc.vc0[p];
+        in.c1 = R.rec.vc.vc1[p];
+        in.c2 = R.rec.vc.vc2[p];
+        if (!R.lam_in_by_id) {
+            in.l0 = R.lp_in[p];
+            in.l1 = R.lp_in[R.np + p];
+            in.l2 = R.lp_in[2 * R.np + p];
+        }
+    }
+}
 
 // DO_G2P: reverse G2P of sub-step k (and P2G of sub-step k+1 if DO_P2G) for
 // the particles recorded as sub-step k's input.  !DO_G2P: reverse P2G of the
 // first sub-step at those particles themselves (v0, C0: their initial v, C).
-template <bool DO_P2G, bool DO_G2P>
+template <bool DO_P2G, bool DO_G2P, int LANES = kRevLanes>
 __global__ void __launch_bounds__(kRevThreads) k_reverse_step(DevParams P, ReverseArgs R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RevSmem &s = *reinterpret_cast<RevSmem *>(smem_raw);
     const int tid = threadIdx.x;
     const EnvParams ep = P.envp[0];
     const int n = P.n, nb = P.nb;
-    const int ntw = ep.ntools * (int)(sizeof(ToolFrame) / 4);
-    if (DO_G2P)
-        for (int q = tid; q < ntw; q += kRevThreads)
-            reinterpret_cast<float *>(s.tools)[q] = reinterpret_cast<const float *>(R.frames)[q];
     float mub = 0.f, lamb = 0.f;
     const uint32_t nact = *R.rec.nact;
+    if (DO_G2P && blockIdx.x == 0 && tid == 0) *R.touch_n = nact;
     for (uint32_t it = blockIdx.x; it < nact * kMaxChunks; it += gridDim.x) {
-        const uint32_t b = R.rec.act[it % nact], chunk = it / nact;
-        const uint2 brng = R.rec.blk[b];
+        const uint32_t ai = it % nact, chunk = it / nact;
+        const uint32_t b = R.rec.act[ai];
+        const uint2 brng = R.rec.blk[ai];
         const uint32_t c0 = chunk * kChunk;
-        if (c0 >= brng.y) continue;                  // uniform over the CTA
+        if (c0 >= brng.y) {                          // uniform over the CTA
+            if (DO_G2P && chunk == 0 && tid < 8) R.touch_list[8 * it + tid] = kNoBlock;
+            continue;
+        }
         const uint2 rng = make_uint2(brng.x + c0, chunk + 1 == kMaxChunks ? brng.y - c0 : min(kChunk, brng.y - c0));
         const int bx = b % nb, by = (b / nb) % nb, bz = b / (nb * nb);
         const int ox = 4 * bx, oy = 4 * by, oz = 4 * bz;
+        // LANES == 3: lanes 3g .. 3g+2 of a warp hold particle g of the warp's ten, one
+        // z-plane of its stencils each; rounds are warp-uniform so that the lane
+        // reductions see every lane of the warp.  LANES == 1: one particle per lane.
+        const int lane = tid & 31, warp = tid >> 5;
+        constexpr uint32_t kPerWarp = LANES == 3 ? 10u : 32u;
+        const int grp = LANES == 3 ? (lane < 30 ? lane / 3 : 9) : lane;
+        const uint32_t end = rng.x + rng.y;
+        // the first round's inputs, loaded now so that they arrive during the tiles
+        const uint32_t base0 = rng.x + kPerWarp * (uint32_t)warp;
+        RevIn in0;
+        load_rev_in<DO_G2P>(R, base0 + (uint32_t)grp < end ? base0 + (uint32_t)grp : rng.x, in0);
         __syncthreads();   // the previous item's tiles are consumed
-        if (DO_G2P && chunk == 0 && tid < 32) {
-            // list the grid blocks this block's scatter reaches, b + {0,1}^3 (lanes 0..7),
-            // with one atomic on the list's count per block
+        // the grid blocks this block's scatter reaches, b + {0,1}^3: threads 0..7 claim
+        // them through the stamps (issued here, the result used at the end of the item)
+        // and fill the block's 8 entries of the touched list (it is b's index in the list)
+        const bool marks = DO_G2P && chunk == 0 && tid < 8;
+        uint32_t tb = kNoBlock, old = R.sv;
+        if (marks) {
             const int tx = bx + (tid & 1), ty = by + ((tid >> 1) & 1), tz = bz + ((tid >> 2) & 1);
-            uint32_t tb = 0;
-            bool fresh = false;
-            if (tid < 8 && tx < nb && ty < nb && tz < nb) {
+            if (tx < nb && ty < nb && tz < nb) {
                 tb = block_id(tx, ty, tz, nb);
-                fresh = atomicExch(&R.stamp[tb], R.sv) != R.sv;
+                old = atomicExch(&R.stamp[tb], R.sv);
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, fresh);
-            uint32_t first = 0;
-            if (tid == 0 && bal) first = atomicAdd(R.touch_count, (uint32_t)__popc(bal));
-            first = __shfl_sync(0xffffffffu, first, 0);
-            if (fresh) R.touch_list[first + __popc(bal & ((1u << tid) - 1u))] = tb;
         }
         if (DO_G2P) {
+            // the grid velocities of sub-step k as its grid operation left them
             for (int q = tid; q < 216; q += kRevThreads) {
                 const int i = ox + q % 6, j = oy + (q / 6) % 6, k = oz + q / 36;
-                float3 v = make_float3(0.f, 0.f, 0.f);
-                if (i < n && j < n && k < n) {
-                    const float4 g = R.Gk[node_addr(i, j, k, nb)];
-                    v = grid_node_update(g.x, g.y, g.z, g.w, i, j, k, P, s.tools, ep.ntools);
-                }
-                s.vtile[q] = make_float4(v.x, v.y, v.z, 0.f);
+                s.vtile[q] = (i < n && j < n && k < n) ? R.rec.vgrid[node_addr(i, j, k, nb)]
+                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         if (DO_P2G) {
@@ -114,18 +148,6 @@ __global__ void __launch_bounds__(kRevThreads) k_reverse_step(DevParams P, Rever
             const float4 g = s.vtile[tile6(b0, b1, b2, ii, jj, kk)];
             return make_float3(g.x, g.y, g.z);
         };
-        // a node's velocity adjoint goes straight to dL/dV_k as one vector
-        // reduction (shared float atomics into an arena were 13% slower overall)
-        auto scatter = [&](int b0, int b1, int b2, int ii, int jj, int kk, float3 val) {
-            const int q = tile6(b0, b1, b2, ii, jj, kk);
-            const int gi = ox + q % 6, gj = oy + (q / 6) % 6, gk = oz + q / 36;
-            if (gi < n && gj < n && gk < n) {
-                float4 *gp = &R.vbar[node_addr(gi, gj, gk, nb)];
-                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(gp), "f"(0.f), "f"(val.x),
-                             "f"(val.y), "f"(val.z)
-                             : "memory");
-            }
-        };
         auto gtile = [&](int b0, int b1, int b2, int ii, int jj, int kk) {
             return s.gbt[(b0 - ox + 1 + ii) + 8 * (b1 - oy + 1 + jj) + 64 * (b2 - oz + 1 + kk)];
         };
@@ -133,33 +155,44 @@ __global__ void __launch_bounds__(kRevThreads) k_reverse_step(DevParams P, Rever
             return R.gbar_next[node_addr(b0 + ii, b1 + jj, b2 + kk, nb)];
         };
         (void)gtile;
-        // three lanes per particle, one z-plane of its stencils each: lanes 3g .. 3g+2
-        // of a warp hold particle g of the warp's ten; rounds are warp-uniform so
-        // that the lane reductions see every lane of the warp
-        const int lane = tid & 31, warp = tid >> 5;
-        const int grp = lane < 30 ? lane / 3 : 9, kk = lane < 30 ? lane % 3 : 0;
-        const ThreeLanes red{3 * grp};
-        const bool lead = lane < 30 && kk == 0;
-        const uint32_t end = rng.x + rng.y;
-        for (uint32_t base = rng.x + 10u * (uint32_t)warp; base < end; base += 10u * (kRevThreads / 32)) {
+        const int kk = LANES == 3 ? (lane < 30 ? lane % 3 : 0) : 0;
+        constexpr int nkk = LANES == 3 ? 1 : 3;
+        using Red = typename std::conditional<LANES == 3, ThreeLanes, OneLane>::type;
+        Red red;
+        if constexpr (LANES == 3) red.l0 = 3 * grp;
+        const bool lead = LANES == 3 ? (lane < 30 && kk == 0) : true;
+        for (uint32_t base = base0; base < end; base += kPerWarp * (kRevThreads / 32)) {
             const uint32_t p0 = base + (uint32_t)grp;
-            const bool active = lane < 30 && p0 < end;
+            const bool active = (LANES == 1 || lane < 30) && p0 < end;
             const uint32_t p = active ? p0 : rng.x;          // inactive lanes compute on a valid particle
-            const float4 xi = R.rec.xi[p];
-            const float4 a0 = R.rec.f0[p], a1 = R.rec.f1[p];
-            const float F[9] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, R.rec.f2[p]};
+            RevIn in;
+            if (base == base0) in = in0;
+            else load_rev_in<DO_G2P>(R, p, in);
+            const float4 xi = in.xi, a0 = in.a0, a1 = in.a1;
+            const float F[9] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, in.f2};
             const float xp[3] = {xi.x, xi.y, xi.z};
-            const size_t id = __float_as_uint(xi.w);
+            const size_t id = min(__float_as_uint(xi.w), R.np - 1u);   // clamped: a record is never read out of range
             float xb[3], vb[3], Cb[9], Fb[9];
+            if (!DO_G2P || R.lam_in_by_id) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) { xb[a] = R.lam.x[3 * id + a]; vb[a] = R.lam.v[3 * id + a]; }
+                for (int a = 0; a < 3; ++a) { xb[a] = R.lam.x[3 * id + a]; vb[a] = R.lam.v[3 * id + a]; }
 #pragma unroll
-            for (int q = 0; q < 9; ++q) { Cb[q] = R.lam.C[9 * id + q]; Fb[q] = R.lam.F[9 * id + q]; }
+                for (int q = 0; q < 9; ++q) { Cb[q] = R.lam.C[9 * id + q]; Fb[q] = R.lam.F[9 * id + q]; }
+            } else {
+                const float4 l0 = in.l0, l1 = in.l1, l2 = in.l2;
+                xb[0] = l0.x; xb[1] = l0.y; xb[2] = l0.z;
+                Fb[0] = l0.w; Fb[1] = l1.x; Fb[2] = l1.y; Fb[3] = l1.z; Fb[4] = l1.w;
+                Fb[5] = l2.x; Fb[6] = l2.y; Fb[7] = l2.z; Fb[8] = l2.w;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) vb[a] = 0.f;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) Cb[q] = 0.f;
+            }
             // the state the reverse P2G differentiates, and where its stencil sits
             float xs[3], vs[3], Cs[9], Fs[9];
             if (DO_G2P) {
                 // v and C after the sub-step as the forward pass computed them
-                const float4 c0 = R.rec.vc.vc0[p], c1 = R.rec.vc.vc1[p], c2 = R.rec.vc.vc2[p];
+                const float4 c0 = in.c0, c1 = in.c1, c2 = in.c2;
                 vs[0] = c0.x; vs[1] = c0.y; vs[2] = c0.z;
                 Cs[0] = c0.w; Cs[1] = c1.x; Cs[2] = c1.y; Cs[3] = c1.z; Cs[4] = c1.w;
                 Cs[5] = c2.x; Cs[6] = c2.y; Cs[7] = c2.z; Cs[8] = c2.w;
@@ -187,10 +220,10 @@ __global__ void __launch_bounds__(kRevThreads) k_reverse_step(DevParams P, Rever
                                      hb[2] - oz >= -1 && hb[2] - oz <= 4;
                 float vbn[3], Cbn[9];
                 if (__all_sync(0xffffffffu, in_tile))
-                    adj_p2g_particle(P, ep, xs, vs, Cs, Fs, gtile, xb, Fb, vbn, Cbn, mub, lamb, kk, 1, red,
+                    adj_p2g_particle(P, ep, xs, vs, Cs, Fs, gtile, xb, Fb, vbn, Cbn, mub, lamb, kk, nkk, red,
                                      lead && active);
                 else
-                    adj_p2g_particle(P, ep, xs, vs, Cs, Fs, gglob, xb, Fb, vbn, Cbn, mub, lamb, kk, 1, red,
+                    adj_p2g_particle(P, ep, xs, vs, Cs, Fs, gglob, xb, Fb, vbn, Cbn, mub, lamb, kk, nkk, red,
                                      lead && active);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) vb[a] += vbn[a];
@@ -198,16 +231,53 @@ __global__ void __launch_bounds__(kRevThreads) k_reverse_step(DevParams P, Rever
                 for (int q = 0; q < 9; ++q) Cb[q] += Cbn[q];
             }
             if (DO_G2P) {
-                float xbn[3], Fbn[9];
-                auto scatter_if = [&](int b0, int b1, int b2, int ii, int jj, int kq, float3 val) {
-                    if (active) scatter(b0, b1, b2, ii, jj, kq, val);
+                // node (i, j, k) sits at node_addr = ax(i) + ay(j) + az(k): the three parts
+                // of this particle's (clamped) stencil nodes, and which lie in the grid
+                uint32_t axo[3], ayo[3], azo[3], okm = 0u;
+                {
+                    uint32_t e2 = 0;
+                    int hb[3];
+                    stencil_axis(xp[0], P.inv_dx, n, hb[0], e2);
+                    stencil_axis(xp[1], P.inv_dx, n, hb[1], e2);
+                    stencil_axis(xp[2], P.inv_dx, n, hb[2], e2);
+                    const int gx = ox + min(max(hb[0] - ox, 0), 3), gy = oy + min(max(hb[1] - oy, 0), 3);
+                    const int gz = oz + min(max(hb[2] - oz, 0), 3);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const uint32_t x = (uint32_t)(gx + i), y = (uint32_t)(gy + i), z = (uint32_t)(gz + i);
+                        axo[i] = 64u * (x >> 2) + (x & 3u);
+                        ayo[i] = 64u * (uint32_t)nb * (y >> 2) + 4u * (y & 3u);
+                        azo[i] = 64u * (uint32_t)nb * (uint32_t)nb * (z >> 2) + 16u * (z & 3u);
+                        okm |= ((x < (uint32_t)n) ? 1u : 0u) << i;
+                        okm |= ((y < (uint32_t)n) ? 1u : 0u) << (3 + i);
+                        okm |= ((z < (uint32_t)n) ? 1u : 0u) << (6 + i);
+                    }
+                    if (!active) okm = 0u;
+                }
+                // a node's velocity adjoint goes straight to dL/dV_k as one vector
+                // reduction (shared float atomics into an arena were 13% slower overall)
+                auto scatter = [&](int, int, int, int ii, int jj, int kq, float3 val) {
+                    if ((okm >> ii) & (okm >> (3 + jj)) & (okm >> (6 + kq)) & 1u) {
+                        float4 *gp = &R.vbar[axo[ii] + ayo[jj] + pick3(azo, kq)];
+                        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(gp), "f"(0.f), "f"(val.x),
+                                     "f"(val.y), "f"(val.z)
+                                     : "memory");
+                    }
                 };
-                adj_g2p_particle(P, xp, F, vel, xb, vb, Cb, Fb, scatter_if, xbn, Fbn, kk, 1, red, Cs);
+                float xbn[3], Fbn[9];
+                adj_g2p_particle(P, xp, F, vel, xb, vb, Cb, Fb, scatter, xbn, Fbn, kk, nkk, red, Cs, vs);
                 if (lead && active) {
+                    if (R.lam_out_by_id) {
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) { R.lam.x[3 * id + a] = xbn[a]; R.lam.v[3 * id + a] = 0.f; }
+                        for (int a = 0; a < 3; ++a) { R.lam.x[3 * id + a] = xbn[a]; R.lam.v[3 * id + a] = 0.f; }
 #pragma unroll
-                    for (int q = 0; q < 9; ++q) { R.lam.F[9 * id + q] = Fbn[q]; R.lam.C[9 * id + q] = 0.f; }
+                        for (int q = 0; q < 9; ++q) { R.lam.F[9 * id + q] = Fbn[q]; R.lam.C[9 * id + q] = 0.f; }
+                    } else {
+                        const uint32_t q = min(R.rec.src[p], R.np - 1u);
+                        R.lp_out[q] = make_float4(xbn[0], xbn[1], xbn[2], Fbn[0]);
+                        R.lp_out[R.np + q] = make_float4(Fbn[1], Fbn[2], Fbn[3], Fbn[4]);
+                        R.lp_out[2 * R.np + q] = make_float4(Fbn[5], Fbn[6], Fbn[7], Fbn[8]);
+                    }
                 }
             } else if (lead && active) {
 #pragma unroll
@@ -216,6 +286,8 @@ __global__ void __launch_bounds__(kRevThreads) k_reverse_step(DevParams P, Rever
                 for (int q = 0; q < 9; ++q) { R.lam.F[9 * id + q] = Fb[q]; R.lam.C[9 * id + q] = Cb[q]; }
             }
         }
+        // the claimed blocks, stored last: the stamp exchanges ran during the item
+        if (marks) R.touch_list[8 * it + tid] = old != R.sv ? tb : kNoBlock;
     }
     if (DO_P2G) {
         // the CTA's part of dL/dmu, dL/dlambda, added to its own pair of the

@@ -42,14 +42,15 @@ void launch_adj_g2p(const DevParams &P, const PState &S, uint32_t n, const float
                     int grid, cudaStream_t st);
 // G: the (m, mv) grid the forward grid operation read; Gb in: velocity
 // adjoint, out: (dL/dm, dL/dmv); tool_bar: ntools x 18 doubles accumulated.
-// Optional block lists (blocks, count): list, the only grid blocks that hold
-// an adjoint; zlist, blocks whose nodes are cleared in zbuf; reset, a list
-// count set to zero.
+// Optional block lists of 8 entries per recorded work-list block (a grid
+// block, or kNoBlock), the number of those work-list blocks at *nlist: list,
+// the only grid blocks that hold an adjoint; zlist, blocks whose nodes are
+// cleared in zbuf.
+constexpr uint32_t kNoBlock = 0xffffffffu;
 struct AdjGridLists {
-    const uint32_t *list = nullptr, *count = nullptr;
-    const uint32_t *zlist = nullptr, *zcount = nullptr;
+    const uint32_t *list = nullptr, *nlist = nullptr;
+    const uint32_t *zlist = nullptr, *znlist = nullptr;
     float4 *zbuf = nullptr;
-    uint32_t *reset = nullptr;
 };
 void launch_adj_grid(const DevParams &P, const float4 *G, const ToolFrame *tools, float4 *Gb, double *tool_bar,
                      int grid, cudaStream_t st, const AdjGridLists &L = AdjGridLists());
@@ -120,29 +121,46 @@ struct FusedBufs {
 // arrays): each block's input particles in block-contiguous order (n
 // entries), per block its (first, count) range, the blocks in work order and
 // their number.
+// Particles are recorded at their output position of the sub-step (inside
+// their block's output range), so that the reverse pass reads the adjoint the
+// later reverse sub-step left at that position with coalesced loads.
 struct StepRecord {
     float4 *xi, *f0, *f1;
     float *f2;
-    uint2 *blk;          // nblocks
+    uint32_t *src;       // each particle's position in the sub-step's input arrays
+    uint2 *blk;          // nblocks: the particle range of the block at each work-list index
     uint32_t *act;       // nblocks
     uint32_t *nact;      // 1
     float4 *grid;        // the grid the sub-step read, over the 6^3 region of every listed block (node layout)
+    float4 *vgrid;       // the grid velocities after the grid operation (.xyz), over the same regions
     VCState vc;          // each particle's v and C after the sub-step (n entries, same order as xi)
 };
 // Inputs and outputs of one reverse sub-step (kernels_reverse.cu).
 struct ReverseArgs {
-    const float4 *Gk;          // grid (m, mv) sub-step k read (do_g2p)
-    const ToolFrame *frames;   // tool frames of sub-step k (do_g2p)
     StepRecord rec;            // sub-step k's input particles by block
     const float4 *gbar_next;   // dL/d(m, mv) of G_{k+1} (do_p2g)
     float4 *vbar;              // dL/dV_k in .yzw, accumulated (do_g2p)
     AdjState lam;              // particle adjoints by particle id
+    // Between the sub-steps of a segment the adjoint of a state is (x, F) only
+    // (G2P does not read v and C, and P2G's part of them stays in the thread),
+    // kept by position as three float4 per particle: (xb, Fb0), Fb1..4, Fb5..8
+    // at [p], [np + p], [2 np + p].  lam_in_by_id: read this sub-step's
+    // incoming adjoint from lam (the segment's last sub-step); otherwise from
+    // lp_in at the particle's recorded (output) position.  lam_out_by_id:
+    // write the outgoing one to lam (the segment's first sub-step); otherwise
+    // to lp_out at the particle's input position (rec.src).
+    const float4 *lp_in;
+    float4 *lp_out;
+    uint32_t np;
+    int lam_in_by_id, lam_out_by_id;
     const float *v0, *C0;      // initial v (n x 3), C (n x 9) by id (do_p2g alone)
     double *lame_part;         // per CTA: its part of dL/dmu, dL/dlambda, accumulated
     // (do_g2p) the grid blocks the sub-step scatters into -- every recorded block
-    // b and b + {0,1}^3 -- listed once in touch_list (count in touch_count, zero on
-    // entry), marked in stamp with value sv
-    uint32_t *stamp, sv, *touch_list, *touch_count;
+    // b and b + {0,1}^3 -- listed once in touch_list (8 entries per work-list
+    // block, kNoBlock where a block is out of the grid or listed by another),
+    // marked in stamp with value sv
+    uint32_t *stamp, sv, *touch_list;
+    uint32_t *touch_n;         // receives the number of work-list blocks (do_g2p)
 };
 // config (MPM_KERNEL_*): 0 = 256 threads, 2 passes per P2G flush; 1 = 256, 1;
 // 2 = 128, 2; 3 = 128, 1
