@@ -302,9 +302,11 @@ mpm_status mpm_autotune(mpm_handle *h, int32_t n_substeps, float *times_ms, int3
  * mpm_tape_backward recomputes the sub-steps in between.  The paper does not
  * differentiate its simulator (Sec. V names differentiable physics as future
  * work); this is the plain reverse mode of the sub-step defined above.
- * Needs a handle with MPM_PIPELINE_SPLIT and one environment (MPM_ERR_STATE
- * otherwise).  poses: host array.  Device memory for the record is taken
- * from the handle's allocator and kept (and reused) until mpm_destroy. */
+ * Needs a handle with one environment (MPM_ERR_STATE otherwise), on either
+ * pipeline.  On MPM_PIPELINE_FUSED the last segment (the sub-steps after the
+ * last checkpoint) is recorded as it runs, so mpm_tape_backward reverses it
+ * without recomputing it.  poses: host array.  Device memory for the record is
+ * taken from the handle's allocator and kept (and reused) until mpm_destroy. */
 mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *poses,
                            int32_t checkpoint_every);
 
@@ -322,6 +324,21 @@ mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *pose
 mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_bar, const float *F_bar,
                              const float *C_bar, int on_device, double *grad_material, double *grad_poses,
                              float *x0_bar, float *v0_bar, float *F0_bar, float *C0_bar);
+
+/* Inspection of a fused-pipeline record (for tests of the reverse mode): the
+ * state sub-step c + j of the rollout started from, where c is the first
+ * sub-step of the last segment (the last multiple of checkpoint_every below
+ * n_substeps) and 0 <= j < n_substeps - c.  These are exactly the states the
+ * reverse pass differentiates at, since it does not recompute that segment.
+ * x (n x 3), v (n x 3), F (n x 9), C (n x 9) by load order; grid: the (m, mv)
+ * grid that sub-step's grid operation read, n_grid^3 x 4 laid out as
+ * mpm_read_grid lays it out (nodes outside the recorded blocks' regions hold
+ * no mass and read as 0).  Any output may be NULL; on_device says where the
+ * outputs live.  MPM_ERR_STATE without such a record: the split pipeline, no
+ * mpm_tape_record, or an mpm_tape_backward since (it replays earlier segments
+ * into the same buffers).  MPM_ERR_ARG for j out of range.  Synchronises. */
+mpm_status mpm_tape_read_substep(mpm_handle *h, int32_t j, float *x, float *v, float *F, float *C, float *grid,
+                                 int on_device);
 
 /* ------------------------------------------------------ without allocation */
 

@@ -1420,6 +1420,60 @@ mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_b
     return MPM_OK;
 }
 
+mpm_status mpm_tape_read_substep(mpm_handle *h, int32_t j, float *x, float *v, float *F, float *C, float *grid,
+                                 int on_device) {
+    mpm_status st = check_handle(h);
+    if (st != MPM_OK) return st;
+    Tape &tp = h->tape;
+    if (!tp.valid || !tp.fused || !tp.last_recorded || tp.n != h->n)
+        return fail(MPM_ERR_STATE, "no recorded segment (a fused-pipeline mpm_tape_record, before mpm_tape_backward)");
+    const int nck = (tp.nsub + tp.ck - 1) / tp.ck, c_last = (nck - 1) * tp.ck, len = tp.nsub - c_last;
+    if (j < 0 || j >= len) return fail(MPM_ERR_ARG, "j outside the last segment of the record");
+    if ((st = poll_error(h, false)) != MPM_OK) return st;
+    const size_t n = (size_t)tp.n;
+    cudaStream_t s = h->stream;
+    // host outputs are staged in the adjoint buffer, which mpm_tape_backward sets anew
+    float *ox = x, *ov = v, *oF = F, *oC = C;
+    if (!on_device) {
+        ox = x ? tp.abar : nullptr;
+        ov = v ? tp.abar + 3 * n : nullptr;
+        oF = F ? tp.abar + 6 * n : nullptr;
+        oC = C ? tp.abar + 15 * n : nullptr;
+    }
+    const StepRecord r = step_record(h, j);
+    if (ox || oF) launch_read_out(PState{r.xi, r.f0, r.f1, r.f2}, r.vc, (uint32_t)n, ox, nullptr, oF, nullptr,
+                                  h->elem_grid, s);
+    if (ov || oC) {
+        if (j > 0) {
+            // v and C as the sub-step before wrote them (its record holds the ids at the same positions)
+            const StepRecord q = step_record(h, j - 1);
+            launch_read_out(PState{q.xi, q.f0, q.f1, q.f2}, q.vc, (uint32_t)n, nullptr, ov, nullptr, oC, h->elem_grid, s);
+        } else {
+            const float *ck = tp.ckpt + (size_t)(nck - 1) * tp.image;     // the segment's checkpoint, by id
+            if (ov) CK(cudaMemcpyAsync(ov, ck + 3 * n, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, s));
+            if (oC) CK(cudaMemcpyAsync(oC, ck + 15 * n, sizeof(float) * 9 * n, cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    if (!on_device) {
+        if (x) CK(cudaMemcpyAsync(x, ox, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+        if (v) CK(cudaMemcpyAsync(v, ov, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+        if (F) CK(cudaMemcpyAsync(F, oF, sizeof(float) * 9 * n, cudaMemcpyDeviceToHost, s));
+        if (C) CK(cudaMemcpyAsync(C, oC, sizeof(float) * 9 * n, cudaMemcpyDeviceToHost, s));
+    }
+    if (grid) {
+        const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
+        if (on_device) {
+            launch_grid_to_dense(h->P.n, h->P.nb, 1, r.grid, reinterpret_cast<float4 *>(grid), h->elem_grid, s);
+        } else {
+            if ((st = ensure_dense(h)) != MPM_OK) return st;
+            launch_grid_to_dense(h->P.n, h->P.nb, 1, r.grid, h->dense, h->elem_grid, s);
+            CK(cudaMemcpyAsync(grid, h->dense, sizeof(float4) * nn, cudaMemcpyDeviceToHost, s));
+        }
+    }
+    CK(cudaGetLastError());
+    return mpm_synchronize(h);
+}
+
 }  // extern "C"
 
 // =========================================================== kernel tuning

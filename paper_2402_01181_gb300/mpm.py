@@ -98,6 +98,8 @@ SIGNATURES = [
     ("mpm_autotune", ct.c_int, [ct.c_void_p, ct.c_int32, _FP, ct.POINTER(ct.c_int32)]),
     ("mpm_tape_backward", ct.c_int, [ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_int,
                                      _DP, _DP, ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]),
+    ("mpm_tape_read_substep", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                                         ct.c_void_p, ct.c_void_p, ct.c_int]),
 ]
 
 
@@ -143,6 +145,7 @@ mpm_extract_surface = lib.mpm_extract_surface
 mpm_get_kernel_config = lib.mpm_get_kernel_config
 mpm_autotune = lib.mpm_autotune
 mpm_tape_backward = lib.mpm_tape_backward
+mpm_tape_read_substep = lib.mpm_tape_read_substep
 
 
 def mpm_last_error() -> str:
@@ -369,6 +372,16 @@ class Sim:
         res = {"E": float(gm[0]), "nu": float(gm[1]), "poses": gp}
         res.update(outs)
         return res
+
+    def tape_read_substep(self, j):
+        """The recorded state (x, v, F, C) and grid of sub-step j of the last
+        segment of a fused-pipeline record (host numpy arrays)."""
+        n, ng = self.n, self.cfg.n_grid
+        out = {k: np.empty((n, c), np.float32) for k, c in (("x", 3), ("v", 3), ("F", 9), ("C", 9))}
+        out["grid"] = np.empty((ng, ng, ng, 4), np.float32)
+        ptrs = [out[k].ctypes.data_as(ct.c_void_p) for k in ("x", "v", "F", "C", "grid")]
+        check(mpm_tape_read_substep(self.h, int(j), *ptrs, 0))
+        return out
 
     def step(self, n_substeps=1):
         check(mpm_step(self.h, int(n_substeps)))
