@@ -120,6 +120,30 @@ static_assert(sizeof(Ctrl) == 7 * 128, "Ctrl: one 128-byte line per counter grou
 // Grid nodes are stored in 4x4x4 blocks (x fastest inside the block and
 // across blocks); every node is a float4 (m, mv_x, mv_y, mv_z) before the
 // grid operation.
+// Programmatic dependent launch (a kernel launched with the programmatic
+// stream serialization attribute): griddep_wait() blocks until the previous
+// kernel in the stream has completed and its memory is visible;
+// griddep_launch_dependents() lets the next such kernel be scheduled once every
+// CTA of this one has called it (or exited).  Both are no-ops for a kernel
+// launched without the attribute.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+// Launch kernel as a programmatic dependent of the stream's previous kernel.
+template <typename... K, typename... A>
+inline void launch_dependent(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);   // a failure is left for cudaGetLastError
+}
+
 __host__ __device__ __forceinline__ uint32_t block_id(int bx, int by, int bz, int nb) {
     return (uint32_t)(bx + nb * (by + nb * bz));
 }

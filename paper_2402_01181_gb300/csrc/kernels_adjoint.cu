@@ -180,17 +180,27 @@ __global__ void __launch_bounds__(kThreads, 3) k_adj_grid(DevParams P, const flo
                                                         const ToolFrame *__restrict__ tools,
                                                         float4 *__restrict__ Gb, double *__restrict__ tool_bar,
                                                         AdjGridLists L) {
-    // the tool frames are read through L1 (no shared copy, so no barrier before
-    // the first node)
+    // a programmatic dependent of the reverse sub-step: its results are read
+    // after the wait; the next reverse sub-step is released after it too
+    griddep_wait();
+    griddep_launch_dependents();
     const int ntools = P.envp[0].ntools;
     const int lo = P.bound, hi = P.n - P.bound;
     const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
     if (!L.list) {
-        // every node; n^3 is a multiple of 64, so whole warps stay in the loop
+        // every node (n^3 is a multiple of 64, so whole warps stay in the loop), the
+        // tool frames from a shared copy
+        __shared__ ToolFrame s_tools[kMaxTools];
+        if (threadIdx.x < ntools * (sizeof(ToolFrame) / 4))
+            reinterpret_cast<float *>(s_tools)[threadIdx.x] = reinterpret_cast<const float *>(tools)[threadIdx.x];
+        __syncthreads();
         const uint32_t total = (uint32_t)P.n * P.n * P.n;
-        for (uint32_t q = gt; q < total; q += stride) adj_grid_node(P, tools, ntools, Gb, tool_bar, q, G[q], Gb[q], lo, hi);
+        for (uint32_t q = gt; q < total; q += stride)
+            adj_grid_node(P, s_tools, ntools, Gb, tool_bar, q, G[q], Gb[q], lo, hi);
         return;
     }
+    // the listed blocks: the tool frames are read through L1 (no shared copy, so
+    // no barrier before the first node)
     // one thread per node of the listed blocks (the 64 threads of an entry read
     // the same entry, so an empty one is skipped by whole warps)
     const uint32_t total = *L.nlist * 512u, zt = L.zlist ? *L.znlist * 512u : 0u;
@@ -262,7 +272,10 @@ void launch_adj_g2p(const DevParams &P, const PState &S, uint32_t n, const float
 }
 void launch_adj_grid(const DevParams &P, const float4 *G, const ToolFrame *tools, float4 *Gb, double *tool_bar,
                      int grid, cudaStream_t st, const AdjGridLists &L) {
-    k_adj_grid<<<grid, kThreads, 0, st>>>(P, G, tools, Gb, tool_bar, L);
+    if (L.list)   // the fused reverse pass: a programmatic dependent of the reverse sub-step
+        launch_dependent(k_adj_grid, grid, kThreads, 0, st, P, G, tools, Gb, tool_bar, L);
+    else
+        k_adj_grid<<<grid, kThreads, 0, st>>>(P, G, tools, Gb, tool_bar, L);
 }
 void launch_adj_p2g(const DevParams &P, const PState &S, const VCState &V, uint32_t n, const float4 *Gb,
                     const AdjState &A, double *lame_bar, int grid, cudaStream_t st) {

@@ -54,8 +54,9 @@ struct RevIn {
     float4 xi, a0, a1, c0, c1, c2, l0, l1, l2;
     float f2;
 };
+// the recorded part (written by the replay, before the previous reverse launch)
 template <bool DO_G2P>
-__device__ __forceinline__ void load_rev_in(const ReverseArgs &R, uint32_t p, RevIn &in) {
+__device__ __forceinline__ void load_rev_rec(const ReverseArgs &R, uint32_t p, RevIn &in) {
     in.xi = R.rec.xi[p];
     in.a0 = R.rec.f0[p];
     in.a1 = R.rec.f1[p];
@@ -64,11 +65,15 @@ __device__ __forceinline__ void load_rev_in(const ReverseArgs &R, uint32_t p, Re
         in.c0 = R.rec.vc.vc0[p];
         in.c1 = R.rec.vc.vc1[p];
         in.c2 = R.rec.vc.vc2[p];
-        if (!R.lam_in_by_id) {
-            in.l0 = R.lp_in[p];
-            in.l1 = R.lp_in[R.np + p];
-            in.l2 = R.lp_in[2 * R.np + p];
-        }
+    }
+}
+// the incoming adjoint by position (written by the previous reverse launch)
+template <bool DO_G2P>
+__device__ __forceinline__ void load_rev_lam(const ReverseArgs &R, uint32_t p, RevIn &in) {
+    if (DO_G2P && !R.lam_in_by_id) {
+        in.l0 = R.lp_in[p];
+        in.l1 = R.lp_in[R.np + p];
+        in.l2 = R.lp_in[2 * R.np + p];
     }
 }
 
@@ -83,6 +88,12 @@ __global__ void __launch_bounds__(kRevThreads) k_reverse_step(DevParams P, Rever
     const EnvParams ep = P.envp[0];
     const int n = P.n, nb = P.nb;
     float mub = 0.f, lamb = 0.f;
+    // Launched as a programmatic dependent of the previous launch: until
+    // griddep_wait() only the record is read (and this sub-step's own list
+    // slot written), so the first item's set-up overlaps the previous launch.
+    // The next launch is released only after the wait, so it overlaps this one
+    // alone (whose list slots and buffers it does not touch before its wait).
+    bool waited = false;
     const uint32_t nact = *R.rec.nact;
     if (DO_G2P && blockIdx.x == 0 && tid == 0) *R.touch_n = nact;
     for (uint32_t it = blockIdx.x; it < nact * kMaxChunks; it += gridDim.x) {
@@ -106,9 +117,24 @@ __global__ void __launch_bounds__(kRevThreads) k_reverse_step(DevParams P, Rever
         const uint32_t end = rng.x + rng.y;
         // the first round's inputs, loaded now so that they arrive during the tiles
         const uint32_t base0 = rng.x + kPerWarp * (uint32_t)warp;
+        const uint32_t pin0 = base0 + (uint32_t)grp < end ? base0 + (uint32_t)grp : rng.x;
         RevIn in0;
-        load_rev_in<DO_G2P>(R, base0 + (uint32_t)grp < end ? base0 + (uint32_t)grp : rng.x, in0);
+        load_rev_rec<DO_G2P>(R, pin0, in0);
         __syncthreads();   // the previous item's tiles are consumed
+        if (DO_G2P) {
+            // the grid velocities of sub-step k as its grid operation left them
+            for (int q = tid; q < 216; q += kRevThreads) {
+                const int i = ox + q % 6, j = oy + (q / 6) % 6, k = oz + q / 36;
+                s.vtile[q] = (i < n && j < n && k < n) ? R.rec.vgrid[node_addr(i, j, k, nb)]
+                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        if (!waited) {
+            griddep_wait();      // the previous launches' results are complete and visible
+            griddep_launch_dependents();
+            waited = true;
+        }
+        load_rev_lam<DO_G2P>(R, pin0, in0);
         // the grid blocks this block's scatter reaches, b + {0,1}^3: threads 0..7 claim
         // them through the stamps (issued here, the result used at the end of the item)
         // and fill the block's 8 entries of the touched list (it is b's index in the list)
@@ -119,14 +145,6 @@ __global__ void __launch_bounds__(kRevThreads) k_reverse_step(DevParams P, Rever
             if (tx < nb && ty < nb && tz < nb) {
                 tb = block_id(tx, ty, tz, nb);
                 old = atomicExch(&R.stamp[tb], R.sv);
-            }
-        }
-        if (DO_G2P) {
-            // the grid velocities of sub-step k as its grid operation left them
-            for (int q = tid; q < 216; q += kRevThreads) {
-                const int i = ox + q % 6, j = oy + (q / 6) % 6, k = oz + q / 36;
-                s.vtile[q] = (i < n && j < n && k < n) ? R.rec.vgrid[node_addr(i, j, k, nb)]
-                                                        : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
         if (DO_P2G) {
@@ -166,8 +184,12 @@ __global__ void __launch_bounds__(kRevThreads) k_reverse_step(DevParams P, Rever
             const bool active = (LANES == 1 || lane < 30) && p0 < end;
             const uint32_t p = active ? p0 : rng.x;          // inactive lanes compute on a valid particle
             RevIn in;
-            if (base == base0) in = in0;
-            else load_rev_in<DO_G2P>(R, p, in);
+            if (base == base0) {
+                in = in0;
+            } else {
+                load_rev_rec<DO_G2P>(R, p, in);
+                load_rev_lam<DO_G2P>(R, p, in);
+            }
             const float4 xi = in.xi, a0 = in.a0, a1 = in.a1;
             const float F[9] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, in.f2};
             const float xp[3] = {xi.x, xi.y, xi.z};
@@ -289,6 +311,7 @@ __global__ void __launch_bounds__(kRevThreads) k_reverse_step(DevParams P, Rever
         // the claimed blocks, stored last: the stamp exchanges ran during the item
         if (marks) R.touch_list[8 * it + tid] = old != R.sv ? tb : kNoBlock;
     }
+    if (!waited) griddep_wait();     // a CTA without particles still adds to its pair below
     if (DO_P2G) {
         // the CTA's part of dL/dmu, dL/dlambda, added to its own pair of the
         // per-CTA partial sums (no two CTAs share a pair, so no atomics)
@@ -328,11 +351,11 @@ void launch_reverse_step(bool do_p2g, bool do_g2p, const DevParams &P, const Rev
                          cudaStream_t st) {
     const size_t bytes = sizeof(RevSmem);
     if (do_p2g && do_g2p)
-        k_reverse_step<true, true><<<grid, kRevThreads, bytes, st>>>(P, R);
+        launch_dependent(k_reverse_step<true, true>, grid, kRevThreads, bytes, st, P, R);
     else if (do_g2p)
-        k_reverse_step<false, true><<<grid, kRevThreads, bytes, st>>>(P, R);
+        launch_dependent(k_reverse_step<false, true>, grid, kRevThreads, bytes, st, P, R);
     else if (do_p2g)
-        k_reverse_step<true, false><<<grid, kRevThreads, bytes, st>>>(P, R);
+        launch_dependent(k_reverse_step<true, false>, grid, kRevThreads, bytes, st, P, R);
 }
 
 }  // namespace gbmpm
