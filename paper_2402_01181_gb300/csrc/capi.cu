@@ -90,8 +90,8 @@ struct Tape {
     bool fused = false;
     float *final_img = nullptr;       // the state after the rollout (restored after the reverse pass)
     size_t cap_final = 0, cap_rs = 0, cap_rsg = 0, cap_rsb = 0, cap_gb = 0;
-    float *rs = nullptr;              // ck x rs_floats(n): one recorded sub-step's particles
-    float4 *rs_grid = nullptr;        // ck x 2 nn: the grid each recorded sub-step read, and its velocities
+    float *rs = nullptr;              // nbuf x ck x rs_floats(n): one recorded sub-step's particles
+    float4 *rs_grid = nullptr;        // nbuf x ck x 2 nn: the grid each recorded sub-step read, and its velocities
     uint32_t *rs_blk = nullptr;       // ck x (2 nblocks block ranges + nblocks work list + 4 counters)
     float4 *gb2 = nullptr;            // second grid adjoint buffer
     // per grid block: a stamp, and two lists ([count, block ...]) of the blocks
@@ -104,6 +104,7 @@ struct Tape {
     float4 *lp = nullptr;             // 2 x 3 n: state adjoints by position within a segment
     size_t cap_lp = 0;
     bool last_recorded = false;       // the record buffers hold the last segment (from the forward pass)
+    int nbuf = 1;                     // record buffers: 2 when there is more than one segment
 };
 
 }  // namespace
@@ -146,6 +147,11 @@ struct mpm_handle {
     int frames_next = 0;
     uint32_t *h_err = nullptr;       // pinned copy of Ctrl::err
     cudaEvent_t ev_err = nullptr, ev_frames[2] = {nullptr, nullptr};
+    // the reverse pass's segment replays run on their own stream, one segment
+    // ahead of the reverse sub-steps: rp_rec[b] marks record buffer b complete,
+    // rp_free[b] its last reader done, rp_go the start of a reverse pass
+    cudaStream_t rp_stream = nullptr;
+    cudaEvent_t rp_rec[2] = {nullptr, nullptr}, rp_free[2] = {nullptr, nullptr}, rp_go = nullptr;
     bool err_pending = false;
     std::vector<HostTool> tools;         // n_envs x MPM_MAX_TOOLS
     std::vector<HostField> fields;       // sampled distance fields, shared by every environment
@@ -231,6 +237,18 @@ void release_all(mpm_handle *h) {
         h->h_frames[b] = nullptr;
         h->ev_frames[b] = nullptr;
     }
+    if (h->rp_stream) {
+        cudaStreamSynchronize(h->rp_stream);
+        cudaStreamDestroy(h->rp_stream);
+        h->rp_stream = nullptr;
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (h->rp_rec[b]) cudaEventDestroy(h->rp_rec[b]);
+        if (h->rp_free[b]) cudaEventDestroy(h->rp_free[b]);
+        h->rp_rec[b] = h->rp_free[b] = nullptr;
+    }
+    if (h->rp_go) cudaEventDestroy(h->rp_go);
+    h->rp_go = nullptr;
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->ev_err) cudaEventDestroy(h->ev_err);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -634,10 +652,10 @@ mpm_status load_impl(mpm_handle *h, const int64_t *counts, const float *x, const
     h->particle_volume = volumes[0];
     h->env_off[0] = 0;
     for (int e = 0; e < h->n_envs; ++e) {
+        if (h->env_vol[e] != (double)volumes[e]) h->envp_dirty = true;   // the particle mass changes
         h->env_vol[e] = volumes[e];
         h->env_off[e + 1] = h->env_off[e] + (uint32_t)counts[e];
     }
-    h->envp_dirty = true;
     // graphs captured the old parameters
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.second);
     h->graphs.clear();
@@ -649,7 +667,9 @@ mpm_status load_impl(mpm_handle *h, const int64_t *counts, const float *x, const
     CK(cudaMemcpyAsync(h->fb.ctrl, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->d_env_off, h->env_off.data(), sizeof(uint32_t) * (h->n_envs + 1), cudaMemcpyHostToDevice,
                        h->stream));
-    CK(cudaStreamSynchronize(h->stream));   // the host Ctrl and input buffers must outlive the copies
+    // host inputs (possibly pinned, so copied asynchronously) must outlive their
+    // copies; c and env_off are pageable, which cudaMemcpyAsync stages at once
+    if (!on_device && n > 0) CK(cudaStreamSynchronize(h->stream));
     mpm_status st = upload_env_params(h);
     if (st != MPM_OK) return st;
     h->step = k0;
@@ -1035,11 +1055,13 @@ size_t rs_floats(int64_t n) { return 24 * (size_t)n + 2 * (((size_t)n + 3) & ~si
 // work list (1 per block) and the list length (padded to 4 words)
 size_t rs_words(const mpm_handle *h) { return 3 * (size_t)h->nblocks + 4; }
 
-StepRecord step_record(mpm_handle *h, int j) {
+// Sub-step j of record buffer buf (segment sg is recorded in buffer sg % nbuf).
+StepRecord step_record(mpm_handle *h, int j, int buf) {
     Tape &tp = h->tape;
     const size_t n = (size_t)tp.n;
-    float *base = tp.rs + (size_t)j * rs_floats(tp.n);
-    uint32_t *w = tp.rs_blk + (size_t)j * rs_words(h);
+    const size_t slot = (size_t)buf * tp.ck + j;
+    float *base = tp.rs + slot * rs_floats(tp.n);
+    uint32_t *w = tp.rs_blk + slot * rs_words(h);
     StepRecord r;
     r.xi = reinterpret_cast<float4 *>(base);
     r.f0 = reinterpret_cast<float4 *>(base + 4 * n);
@@ -1053,7 +1075,7 @@ StepRecord step_record(mpm_handle *h, int j) {
     r.act = w + 2 * (size_t)h->nblocks;
     r.nact = w + 3 * (size_t)h->nblocks;
     const size_t nn = (size_t)h->P.n * h->P.n * h->P.n;
-    r.grid = tp.rs_grid + 2 * (size_t)j * nn;
+    r.grid = tp.rs_grid + 2 * slot * nn;
     r.vgrid = r.grid + nn;
     return r;
 }
@@ -1079,12 +1101,46 @@ mpm_status load_image(mpm_handle *h, const float *img) {
     return st;
 }
 
+// The replay stream and its events, created on first use.
+mpm_status ensure_replay_stream(mpm_handle *h) {
+    if (h->rp_stream) return MPM_OK;
+    CK(cudaStreamCreateWithFlags(&h->rp_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        CK(cudaEventCreateWithFlags(&h->rp_rec[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->rp_free[b], cudaEventDisableTiming));
+    }
+    CK(cudaEventCreateWithFlags(&h->rp_go, cudaEventDisableTiming));
+    return MPM_OK;
+}
+
+// Replay segment sg from its checkpoint with recording sub-steps, into record
+// buffer sg % nbuf, on stream r (the load path runs there too).
+mpm_status replay_segment(mpm_handle *h, int sg, cudaStream_t r) {
+    Tape &tp = h->tape;
+    const int c0 = sg * tp.ck, len = std::min(tp.ck, tp.nsub - c0), b = sg % tp.nbuf;
+    cudaStream_t keep = h->stream;
+    h->stream = r;
+    mpm_status st = load_image(h, tp.ckpt + (size_t)sg * tp.image);
+    if (st == MPM_OK) {
+        for (int j = 0; j < len; ++j) {
+            launch_fused_step_record(h->P, h->fb, tp.frames + (size_t)(c0 + j) * tp.ntools, step_record(h, j, b),
+                                     record_grid(h), r);
+            h->step += 1u;
+        }
+    }
+    h->stream = keep;
+    return st;
+}
+
 // Reverse pass of a rollout recorded on the fused pipeline.  Segment by
-// segment, last first: restore the segment's checkpoint, replay it with
-// recording sub-steps, then reverse its sub-steps with the block-sorted
-// reverse sub-step (G2P of sub-step k and P2G of sub-step k+1) and the
-// reverse grid operation of sub-step k; finally the reverse of the first
-// sub-step's P2G.  The live state is restored to the rollout's end.
+// segment, last first: reverse the segment's sub-steps from its record with
+// the block-sorted reverse sub-step (G2P of sub-step k and P2G of sub-step
+// k+1) and the reverse grid operation of sub-step k; finally the reverse of
+// the first sub-step's P2G.  The record of a segment is made by replaying it
+// from its checkpoint; with two record buffers the replays run on their own
+// stream one segment ahead, beside the reverse of the segment after.  The
+// last segment's record comes from the forward pass.  The live state is
+// restored to the rollout's end.
 mpm_status fused_reverse(mpm_handle *h, const AdjState &A, int nck) {
     Tape &tp = h->tape;
     const int nt = tp.ntools;
@@ -1112,23 +1168,38 @@ mpm_status fused_reverse(mpm_handle *h, const AdjState &A, int nck) {
     // the reverse grid operation: one wave of 3 CTAs per SM (a node per thread
     // over 8 list entries per work-list block, most of them empty)
     const int adj_grid_ctas = 3 * h->num_sms;
+    const bool have_last = tp.last_recorded;
+    tp.last_recorded = false;     // the replays below overwrite the record buffers
+    const bool ahead = tp.nbuf == 2;
+    cudaStream_t r = s;
+    if (ahead) {
+        if ((st = ensure_replay_stream(h)) != MPM_OK) return st;
+        r = h->rp_stream;
+        CK(cudaEventRecord(h->rp_go, s));       // replays follow everything issued so far
+        CK(cudaStreamWaitEvent(r, h->rp_go, 0));
+        // the first segments: the last one (unless the forward pass recorded it)
+        // and the one before it, into the two buffers
+        for (int sg = nck - 1; sg >= std::max(nck - 2, 0); --sg) {
+            if (sg == nck - 1 && have_last) continue;
+            if ((st = replay_segment(h, sg, r)) != MPM_OK) return st;
+            CK(cudaEventRecord(h->rp_rec[sg % 2], r));
+        }
+    }
     for (int sg = nck - 1; sg >= 0; --sg) {
-        const int c0 = sg * tp.ck, len = std::min(tp.ck, tp.nsub - c0);
-        if (sg == nck - 1 && tp.last_recorded) {
-            tp.last_recorded = false;     // the replays below overwrite it
-        } else {
-            if ((st = load_image(h, tp.ckpt + (size_t)sg * tp.image)) != MPM_OK) return st;
-            for (int j = 0; j < len; ++j) {
-                launch_fused_step_record(h->P, h->fb, tp.frames + (size_t)(c0 + j) * nt, step_record(h, j),
-                                         record_grid(h), s);
-                h->step += 1u;
+        const int c0 = sg * tp.ck, len = std::min(tp.ck, tp.nsub - c0), b = sg % tp.nbuf;
+        const bool replayed = !(sg == nck - 1 && have_last);
+        if (replayed) {
+            if (ahead) {
+                CK(cudaStreamWaitEvent(s, h->rp_rec[b], 0));
+            } else if ((st = replay_segment(h, sg, s)) != MPM_OK) {
+                return st;
             }
         }
         for (int j = len - 1; j >= 0; --j) {
             const int k = c0 + j;
             const int sk = k % 3, sk1 = (k + 1) % 3;
             ReverseArgs R{};
-            R.rec = step_record(h, j);
+            R.rec = step_record(h, j, b);
             R.gbar_next = gnext;
             R.vbar = gcur;
             R.lam = A;
@@ -1142,7 +1213,9 @@ mpm_status fused_reverse(mpm_handle *h, const AdjState &A, int nck) {
             R.sv = ++tp.touch_sv;
             R.touch_list = lists + (size_t)sk * 8 * nbk;
             R.touch_n = counts + sk;
-            launch_reverse_step(k + 1 < tp.nsub, true, h->P, R, h->rev_grid, s);
+            // a segment's first reverse launch follows its replay (and the wait for it)
+            // in full; the others are programmatic dependents of the launch before
+            launch_reverse_step(k + 1 < tp.nsub, true, h->P, R, h->rev_grid, s, j < len - 1);
             AdjGridLists L;
             L.list = R.touch_list;
             L.nlist = R.touch_n;
@@ -1154,10 +1227,17 @@ mpm_status fused_reverse(mpm_handle *h, const AdjState &A, int nck) {
             std::swap(gnext, gcur);
             std::swap(lp_in, lp_out);
         }
+        if (ahead && sg >= 2) {
+            // buffer b is free once this segment's reverse is done: replay sg - 2 into it
+            CK(cudaEventRecord(h->rp_free[b], s));
+            CK(cudaStreamWaitEvent(r, h->rp_free[b], 0));
+            if ((st = replay_segment(h, sg - 2, r)) != MPM_OK) return st;
+            CK(cudaEventRecord(h->rp_rec[b], r));
+        }
     }
     // the first sub-step's P2G at the initial state (its v and C from checkpoint 0)
     ReverseArgs R{};
-    R.rec = step_record(h, 0);
+    R.rec = step_record(h, 0, 0);
     R.gbar_next = gnext;
     R.lam = A;
     R.v0 = tp.ckpt + 3 * n;
@@ -1166,7 +1246,7 @@ mpm_status fused_reverse(mpm_handle *h, const AdjState &A, int nck) {
     R.lam_in_by_id = 1;
     R.lam_out_by_id = 1;
     R.lame_part = tp.lame_part;
-    launch_reverse_step(true, false, h->P, R, h->rev_grid, s);
+    launch_reverse_step(true, false, h->P, R, h->rev_grid, s, true);
     CK(cudaGetLastError());
     return load_image(h, tp.final_img);
 }
@@ -1206,16 +1286,20 @@ mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *pose
         tp.image = 24 * (size_t)n;
         if ((st = ensure(h, &tp.ckpt, &tp.cap_ckpt, tp.image * nck)) != MPM_OK) return st;
         if ((st = ensure(h, &tp.final_img, &tp.cap_final, tp.image)) != MPM_OK) return st;
-        if ((st = ensure(h, &tp.rs, &tp.cap_rs, rs_floats(n) * ck)) != MPM_OK) return st;
-        if (tp.cap_rsg < 2 * nn * ck) {
+        // two record buffers when there are several segments: the reverse pass
+        // replays a segment into one while it reverses the one in the other
+        const int nbuf = nck > 1 ? 2 : 1;
+        if ((st = ensure(h, &tp.rs, &tp.cap_rs, rs_floats(n) * ck * nbuf)) != MPM_OK) return st;
+        if (tp.cap_rsg < 2 * nn * ck * nbuf) {
             // recorded sub-steps write the grid (before and after the grid operation)
             // over their blocks' regions only; the reverse grid operation also reads the
             // rest of the blocks it lists, where it needs finite values (its adjoint
             // there is zero)
-            if ((st = ensure(h, &tp.rs_grid, &tp.cap_rsg, 2 * nn * ck)) != MPM_OK) return st;
-            CK(cudaMemsetAsync(tp.rs_grid, 0, sizeof(float4) * 2 * nn * ck, h->stream));
+            if ((st = ensure(h, &tp.rs_grid, &tp.cap_rsg, 2 * nn * ck * nbuf)) != MPM_OK) return st;
+            CK(cudaMemsetAsync(tp.rs_grid, 0, sizeof(float4) * 2 * nn * ck * nbuf, h->stream));
         }
-        if ((st = ensure(h, &tp.rs_blk, &tp.cap_rsb, rs_words(h) * ck)) != MPM_OK) return st;
+        if ((st = ensure(h, &tp.rs_blk, &tp.cap_rsb, rs_words(h) * ck * nbuf)) != MPM_OK) return st;
+        tp.nbuf = nbuf;
         if ((st = ensure(h, &tp.gbar, &tp.cap_gb, nn)) != MPM_OK) return st;
         size_t one = tp.cap_gb;
         if ((st = ensure(h, &tp.gb2, &one, nn)) != MPM_OK) return st;
@@ -1257,13 +1341,14 @@ mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *pose
         // checkpoints by particle id; v and C of a checkpointed state are written by
         // the sub-step before it.  The last segment runs with recording sub-steps,
         // so that the reverse pass starts without replaying it (step_record lays
-        // the records out for tp.n particles).
+        // the records out for tp.n particles and tp.ck sub-steps per buffer).
         tp.n = n;
-        const int c_last = (nck - 1) * ck;
+        tp.ck = ck;
+        const int c_last = (nck - 1) * ck, b_last = (nck - 1) % tp.nbuf;
         for (int k = 0; k < n_substeps; ++k) {
             if (k % ck == 0) id_image(h, tp.ckpt + (size_t)(k / ck) * tp.image);
             if (k >= c_last) {
-                launch_fused_step_record(h->P, h->fb, tp.frames + (size_t)k * nt, step_record(h, k - c_last),
+                launch_fused_step_record(h->P, h->fb, tp.frames + (size_t)k * nt, step_record(h, k - c_last, b_last),
                                          record_grid(h), h->stream);
             } else {
                 // the configuration the reverse pass replays segments with, so that the
@@ -1276,7 +1361,7 @@ mpm_status mpm_tape_record(mpm_handle *h, int32_t n_substeps, const double *pose
         }
         // the last sub-step kept v and C in its record, by output position: they
         // become the live state's
-        const VCState rv = step_record(h, n_substeps - 1 - c_last).vc;
+        const VCState rv = step_record(h, n_substeps - 1 - c_last, b_last).vc;
         CK(cudaMemcpyAsync(h->fb.vc.vc0, rv.vc0, 16 * (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
         CK(cudaMemcpyAsync(h->fb.vc.vc1, rv.vc1, 16 * (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
         CK(cudaMemcpyAsync(h->fb.vc.vc2, rv.vc2, 16 * (size_t)n, cudaMemcpyDeviceToDevice, h->stream));
@@ -1440,13 +1525,14 @@ mpm_status mpm_tape_read_substep(mpm_handle *h, int32_t j, float *x, float *v, f
         oF = F ? tp.abar + 6 * n : nullptr;
         oC = C ? tp.abar + 15 * n : nullptr;
     }
-    const StepRecord r = step_record(h, j);
+    const int b = (nck - 1) % tp.nbuf;
+    const StepRecord r = step_record(h, j, b);
     if (ox || oF) launch_read_out(PState{r.xi, r.f0, r.f1, r.f2}, r.vc, (uint32_t)n, ox, nullptr, oF, nullptr,
                                   h->elem_grid, s);
     if (ov || oC) {
         if (j > 0) {
             // v and C as the sub-step before wrote them (its record holds the ids at the same positions)
-            const StepRecord q = step_record(h, j - 1);
+            const StepRecord q = step_record(h, j - 1, b);
             launch_read_out(PState{q.xi, q.f0, q.f1, q.f2}, q.vc, (uint32_t)n, nullptr, ov, nullptr, oC, h->elem_grid, s);
         } else {
             const float *ck = tp.ckpt + (size_t)(nck - 1) * tp.image;     // the segment's checkpoint, by id

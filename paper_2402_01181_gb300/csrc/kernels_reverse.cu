@@ -348,14 +348,20 @@ int reverse_step_ctas_per_sm() {
 }
 
 void launch_reverse_step(bool do_p2g, bool do_g2p, const DevParams &P, const ReverseArgs &R, int grid,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool dependent) {
     const size_t bytes = sizeof(RevSmem);
+    auto go = [&](auto kernel) {
+        if (dependent)
+            launch_dependent(kernel, grid, kRevThreads, bytes, st, P, R);
+        else
+            kernel<<<grid, kRevThreads, bytes, st>>>(P, R);
+    };
     if (do_p2g && do_g2p)
-        launch_dependent(k_reverse_step<true, true>, grid, kRevThreads, bytes, st, P, R);
+        go(k_reverse_step<true, true>);
     else if (do_g2p)
-        launch_dependent(k_reverse_step<false, true>, grid, kRevThreads, bytes, st, P, R);
+        go(k_reverse_step<false, true>);
     else if (do_p2g)
-        launch_dependent(k_reverse_step<true, false>, grid, kRevThreads, bytes, st, P, R);
+        go(k_reverse_step<true, false>);
 }
 
 }  // namespace gbmpm

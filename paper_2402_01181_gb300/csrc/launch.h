@@ -65,9 +65,11 @@ struct ReverseArgs;
 int reverse_step_ctas_per_sm();
 // do_p2g && do_g2p: reverse of G2P of sub-step k and P2G of sub-step k+1;
 // do_g2p alone: the last sub-step of a rollout; do_p2g alone: the reverse of
-// the first sub-step's P2G at the initial state.
+// the first sub-step's P2G at the initial state.  dependent: launched as a
+// programmatic dependent of the stream's previous kernel (which then must be
+// the only work it depends on: its set-up reads the record before waiting).
 void launch_reverse_step(bool do_p2g, bool do_g2p, const DevParams &P, const ReverseArgs &R, int grid,
-                         cudaStream_t st);
+                         cudaStream_t st, bool dependent);
 
 // kernels_surface.cu: iso-surface of the grid density m / (rho dx^3) of
 // environment env.  counts: (n-1)^3 + 1 entries, left holding the exclusive
