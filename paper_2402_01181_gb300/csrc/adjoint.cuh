@@ -114,7 +114,9 @@ __device__ __forceinline__ void stencil_axes(const DevParams &P, const float xp[
 // velocity adjoint of every stencil node to scatter(ii, jj, kk, value) and
 // returns G2P's part of the adjoint of x and F (v and C do not enter G2P).
 // The stencil's z-planes kk0 .. kk0+nkk-1 are this thread's; red sums the
-// partials over the threads that share the particle.  Cnew and vnew, if both
+// partials over the threads that share the particle (FULL: all three, with the
+// z-planes unrolled, for callers whose node accessors load from global
+// memory).  Cnew and vnew, if both
 // given, are the particle's C and v after the sub-step (kept by the forward
 // pass), which spares the recomputation of Eqs. 8-9's sums.
 //
@@ -123,7 +125,7 @@ __device__ __forceinline__ void stencil_axes(const DevParams &P, const float xp[
 // w_i val_i.  The adjoint of x_p is sum_i grad w_i (V_i . val_i) from the
 // weights, plus -K Cbar^T sum_i w_i V_i = -K Cbar^T v from the offsets
 // x_i - x_p, since sum_i w_i V_i is the particle's new velocity (Eq. 8).
-template <class VelAt, class Scatter, class Red = OneLane>
+template <class VelAt, class Scatter, class Red = OneLane, bool FULL = false>
 __device__ __forceinline__ void adj_g2p_particle(const DevParams &P, const float xp[3], const float F[9], VelAt vel,
                                                  const float xbo[3], const float vbo[3], const float Cbo[9],
                                                  const float Fbo[9], Scatter scatter, float xbn[3], float Fbn[9],
@@ -144,8 +146,8 @@ __device__ __forceinline__ void adj_g2p_particle(const DevParams &P, const float
         float Bm[9], vs[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < 9; ++q) Bm[q] = 0.f;
-#pragma unroll 1
-        for (int kk = kk0; kk < kk0 + nkk; ++kk) {
+#pragma unroll(FULL ? 3 : 1)
+        for (int kk = FULL ? 0 : kk0; kk < (FULL ? 3 : kk0 + nkk); ++kk) {
             const float wz = pick3(S.w[2], kk), dz = pick3(S.dp[2], kk);
 #pragma unroll
             for (int jj = 0; jj < 3; ++jj)
@@ -188,8 +190,8 @@ __device__ __forceinline__ void adj_g2p_particle(const DevParams &P, const float
 #pragma unroll
     for (int q = 0; q < 9; ++q) Kc[q] = K * Cbt[q];
     float xnode[3] = {0.f, 0.f, 0.f};
-#pragma unroll 1
-    for (int kk = kk0; kk < kk0 + nkk; ++kk) {
+#pragma unroll(FULL ? 3 : 1)
+    for (int kk = FULL ? 0 : kk0; kk < (FULL ? 3 : kk0 + nkk); ++kk) {
         const float wz = pick3(S.w[2], kk), dwz = pick3(S.dw[2], kk), dz = pick3(S.dp[2], kk);
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
@@ -222,13 +224,14 @@ __device__ __forceinline__ void adj_g2p_particle(const DevParams &P, const float
 // Fb, returns the adjoint of v and C, and adds to mub, lamb the particle's
 // part of dL/dmu and dL/dlambda (only if lead: one of the threads that share
 // the particle).  The stencil's z-planes kk0 .. kk0+nkk-1 are this thread's;
-// red sums the partials over the threads that share the particle.
+// red sums the partials over the threads that share the particle (FULL: all
+// three, unrolled).
 //
 // Node i receives w_i (m, m v + A (x_i - x_p)) with A = m C - dt V0 (4/dx^2) tau.
 // With S = sum_i w_i mvbar_i: vbar = m S, Abar = sum_i w_i mvbar_i (x_i - x_p)^T,
 // and the adjoint of x_p is sum_i grad w_i (mbar_i m + mvbar_i . mom_i) from the
 // weights plus -A^T S from the offsets.
-template <class GbarAt, class Red = OneLane>
+template <class GbarAt, class Red = OneLane, bool FULL = false>
 __device__ __forceinline__ void adj_p2g_particle(const DevParams &P, const EnvParams &ep, const float xp[3],
                                                  const float vp[3], const float C[9], const float F[9], GbarAt gbar,
                                                  float xb[3], float Fb[9], float vb[3], float Cb[9], float &mub,
@@ -248,8 +251,8 @@ __device__ __forceinline__ void adj_p2g_particle(const DevParams &P, const EnvPa
     float Ab[9], Sm[3] = {0.f, 0.f, 0.f}, xbp[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < 9; ++q) Ab[q] = 0.f;
-#pragma unroll 1
-    for (int kk = kk0; kk < kk0 + nkk; ++kk) {
+#pragma unroll(FULL ? 3 : 1)
+    for (int kk = FULL ? 0 : kk0; kk < (FULL ? 3 : kk0 + nkk); ++kk) {
         const float wz = pick3(S.w[2], kk), dwz = pick3(S.dw[2], kk), dz = pick3(S.dp[2], kk);
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {

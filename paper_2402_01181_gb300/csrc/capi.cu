@@ -1446,8 +1446,16 @@ mpm_status mpm_tape_backward(mpm_handle *h, const float *x_bar, const float *v_b
             image_views(tp.seg + (size_t)j * tp.image, n, Sj, Vj);
             const float4 *Gj = tp.seg_grid + (size_t)j * nn, *Uj = tp.seg_vel + (size_t)j * nn;
             const ToolFrame *fr = tp.frames + (size_t)k * nt;
+            // v and C after sub-step k: the next image of the segment or the next
+            // checkpoint (after the last sub-step none is kept: formed again)
+            VCState Vk1{};
+            PState Sk1;
+            if (j + 1 < len)
+                image_views(tp.seg + (size_t)(j + 1) * tp.image, n, Sk1, Vk1);
+            else if (sg + 1 < nck)
+                image_views(tp.ckpt + (size_t)(sg + 1) * tp.image, n, Sk1, Vk1);
             CK(cudaMemsetAsync(tp.gbar, 0, sizeof(float4) * nn, s));
-            launch_adj_g2p(h->P, Sj, (uint32_t)n, Uj, A, tp.gbar, h->elem_grid, s);
+            launch_adj_g2p(h->P, Sj, (uint32_t)n, Uj, A, tp.gbar, Vk1, h->elem_grid, s);
             launch_adj_grid(h->P, Gj, fr, tp.gbar, tp.red + 2 + (size_t)k * nt * 18, h->elem_grid, s);
             launch_adj_p2g(h->P, Sj, Vj, (uint32_t)n, tp.gbar, A, tp.red, h->elem_grid, s);
         }

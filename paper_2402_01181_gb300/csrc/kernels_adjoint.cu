@@ -28,7 +28,7 @@ constexpr int kThreads = 256;
 // (x, F); v and C do not enter G2P, so their adjoints are cleared here.
 __global__ void __launch_bounds__(kThreads) k_adj_g2p(DevParams P, PState S, uint32_t n,
                                                        const float4 *__restrict__ Gv, AdjState A,
-                                                       float4 *__restrict__ Gb) {
+                                                       float4 *__restrict__ Gb, VCState Vn) {
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const float4 xi = S.xi[s];
         const float xp[3] = {xi.x, xi.y, xi.z};
@@ -48,7 +48,18 @@ __global__ void __launch_bounds__(kThreads) k_adj_g2p(DevParams P, PState S, uin
             atomicAdd(&Gb[node_addr(bx + ii, by + jj, bz + kk, nb)], make_float4(0.f, v.x, v.y, v.z));
         };
         float xbn[3], Fbn[9];
-        adj_g2p_particle(P, xp, F, vel, xbo, vbo, Cbo, Fbo, scatter, xbn, Fbn);
+        if (Vn.vc0) {
+            // v and C after the sub-step, as the forward pass wrote them
+            const float4 c0 = Vn.vc0[s], c1 = Vn.vc1[s], c2 = Vn.vc2[s];
+            const float vnew[3] = {c0.x, c0.y, c0.z};
+            const float Cnew[9] = {c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
+            adj_g2p_particle<decltype(vel), decltype(scatter), OneLane, true>(P, xp, F, vel, xbo, vbo, Cbo, Fbo,
+                                                                              scatter, xbn, Fbn, 0, 3, OneLane(),
+                                                                              Cnew, vnew);
+        } else {
+            adj_g2p_particle<decltype(vel), decltype(scatter), OneLane, true>(P, xp, F, vel, xbo, vbo, Cbo, Fbo,
+                                                                              scatter, xbn, Fbn);
+        }
 #pragma unroll
         for (int a = 0; a < 3; ++a) { A.x[3 * (size_t)s + a] = xbn[a]; A.v[3 * (size_t)s + a] = 0.f; }
 #pragma unroll
@@ -242,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_p2g(DevParams P, PState S, VCS
             for (int a = 0; a < 3; ++a) xb[a] = A.x[3 * (size_t)s + a];
 #pragma unroll
             for (int q = 0; q < 9; ++q) Fb[q] = A.F[9 * (size_t)s + q];
-            adj_p2g_particle(P, ep, xp, vp, C, F, gbar, xb, Fb, vb, Cb, mub, lamb);
+            adj_p2g_particle<decltype(gbar), OneLane, true>(P, ep, xp, vp, C, F, gbar, xb, Fb, vb, Cb, mub, lamb);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 A.x[3 * (size_t)s + a] = xb[a];
@@ -266,9 +277,9 @@ __global__ void __launch_bounds__(kThreads) k_adj_p2g(DevParams P, PState S, VCS
 }  // namespace
 
 void launch_adj_g2p(const DevParams &P, const PState &S, uint32_t n, const float4 *Gv, const AdjState &A, float4 *Gb,
-                    int grid, cudaStream_t st) {
+                    const VCState &Vnext, int grid, cudaStream_t st) {
     if (n == 0) return;
-    k_adj_g2p<<<grid, kThreads, 0, st>>>(P, S, n, Gv, A, Gb);
+    k_adj_g2p<<<grid, kThreads, 0, st>>>(P, S, n, Gv, A, Gb, Vnext);
 }
 void launch_adj_grid(const DevParams &P, const float4 *G, const ToolFrame *tools, float4 *Gb, double *tool_bar,
                      int grid, cudaStream_t st, const AdjGridLists &L) {

@@ -37,9 +37,11 @@ struct AdjState {
     float *F;   // n x 9
 };
 // Gv: grid after the forward grid operation (.yzw = velocity); Gb zeroed on
-// entry, receives dL/d(grid velocity) in .yzw.
+// entry, receives dL/d(grid velocity) in .yzw.  Vnext: v and C after the
+// sub-step as the forward pass wrote them (same particle order as S), or
+// null arrays to form them again from Gv.
 void launch_adj_g2p(const DevParams &P, const PState &S, uint32_t n, const float4 *Gv, const AdjState &A, float4 *Gb,
-                    int grid, cudaStream_t st);
+                    const VCState &Vnext, int grid, cudaStream_t st);
 // G: the (m, mv) grid the forward grid operation read; Gb in: velocity
 // adjoint, out: (dL/dm, dL/dmv); tool_bar: ntools x 18 doubles accumulated.
 // Optional block lists of 8 entries per recorded work-list block (a grid
