@@ -1222,6 +1222,10 @@ mpm_status fused_reverse(mpm_handle *h, const AdjState &A, int nck) {
             L.zlist = lists + (size_t)sk1 * 8 * nbk;
             L.znlist = counts + sk1;
             L.zbuf = gnext;
+            if (j > 0) {
+                L.prefetch = step_record(h, j - 1, b).xi;     // sub-step k-1's particles, one slab
+                L.prefetch_bytes = sizeof(float) * rs_floats(tp.n);
+            }
             launch_adj_grid(h->P, R.rec.grid, tp.frames + (size_t)k * nt, gcur, tp.red + 2 + (size_t)k * nt * 18,
                             adj_grid_ctas, s, L);
             std::swap(gnext, gcur);

@@ -191,6 +191,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_adj_grid(DevParams P, const flo
                                                         const ToolFrame *__restrict__ tools,
                                                         float4 *__restrict__ Gb, double *__restrict__ tool_bar,
                                                         AdjGridLists L) {
+    // the next reverse sub-step's record was written a segment's replay ago and
+    // has left L2: start bringing it back (independent of the previous launch)
+    if (L.prefetch) {
+        const char *pf = static_cast<const char *>(L.prefetch);
+        for (size_t off = (size_t)(blockIdx.x * blockDim.x + threadIdx.x) * 128u; off < L.prefetch_bytes;
+             off += (size_t)gridDim.x * blockDim.x * 128u)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(pf + off));
+    }
     // a programmatic dependent of the reverse sub-step: its results are read
     // after the wait; the next reverse sub-step is released after it too
     griddep_wait();

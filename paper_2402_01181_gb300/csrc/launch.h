@@ -53,6 +53,10 @@ struct AdjGridLists {
     const uint32_t *list = nullptr, *nlist = nullptr;
     const uint32_t *zlist = nullptr, *znlist = nullptr;
     float4 *zbuf = nullptr;
+    // a byte range to bring into L2 for the next launch (the next reverse
+    // sub-step's particle record), or none
+    const void *prefetch = nullptr;
+    size_t prefetch_bytes = 0;
 };
 void launch_adj_grid(const DevParams &P, const float4 *G, const ToolFrame *tools, float4 *Gb, double *tool_bar,
                      int grid, cudaStream_t st, const AdjGridLists &L = AdjGridLists());
