@@ -200,6 +200,8 @@ __device__ __forceinline__ void adj_g2p_particle(const DevParams &P, const float
             float rv[3];                                           // val along the row, less its x part
 #pragma unroll
             for (int a = 0; a < 3; ++a) rv[a] = fmaf(Kc[3 * a + 2], dz, fmaf(Kc[3 * a + 1], dy, vbt[a]));
+            // the weight-gradient terms of the row: sum_ii dw_x sdot and sum_ii w_x sdot
+            float sdw = 0.f, sw = 0.f;
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii) {
                 const float wg = S.w[0][ii] * wyz;
@@ -208,10 +210,12 @@ __device__ __forceinline__ void adj_g2p_particle(const DevParams &P, const float
                 const float v0 = fmaf(Kc[0], d0, rv[0]), v1 = fmaf(Kc[3], d0, rv[1]), v2 = fmaf(Kc[6], d0, rv[2]);
                 const float sdot = fmaf(g.z, v2, fmaf(g.y, v1, g.x * v0));      // Eqs. 8-9
                 scatter(S.b[0], S.b[1], S.b[2], ii, jj, kk, make_float3(wg * v0, wg * v1, wg * v2));
-                xnode[0] = fmaf(S.dw[0][ii] * wyz, sdot, xnode[0]);
-                xnode[1] = fmaf(S.w[0][ii] * dwyz, sdot, xnode[1]);
-                xnode[2] = fmaf(S.w[0][ii] * wydz, sdot, xnode[2]);
+                sdw = fmaf(S.dw[0][ii], sdot, sdw);
+                sw = fmaf(S.w[0][ii], sdot, sw);
             }
+            xnode[0] = fmaf(wyz, sdw, xnode[0]);
+            xnode[1] = fmaf(dwyz, sw, xnode[1]);
+            xnode[2] = fmaf(wydz, sw, xnode[2]);
         }
     }
 #pragma unroll
@@ -258,7 +262,7 @@ __device__ __forceinline__ void adj_p2g_particle(const DevParams &P, const EnvPa
         for (int jj = 0; jj < 3; ++jj) {
             const float wyz = S.w[1][jj] * wz, dwyz = S.dw[1][jj] * wz, wydz = S.w[1][jj] * dwz;
             const float dy = S.dp[1][jj];
-            float rm[3], R0[3] = {0.f, 0.f, 0.f}, R1[3] = {0.f, 0.f, 0.f};
+            float rm[3], R0[3] = {0.f, 0.f, 0.f}, R1[3] = {0.f, 0.f, 0.f}, sdw = 0.f, sw = 0.f;
 #pragma unroll
             for (int a = 0; a < 3; ++a) rm[a] = fmaf(Am[3 * a + 2], dz, fmaf(Am[3 * a + 1], dy, mv[a]));
 #pragma unroll
@@ -275,10 +279,12 @@ __device__ __forceinline__ void adj_p2g_particle(const DevParams &P, const EnvPa
                     R0[a] += t;
                     R1[a] = fmaf(t, d0, R1[a]);
                 }
-                xbp[0] = fmaf(S.dw[0][ii] * wyz, sdot, xbp[0]);
-                xbp[1] = fmaf(S.w[0][ii] * dwyz, sdot, xbp[1]);
-                xbp[2] = fmaf(S.w[0][ii] * wydz, sdot, xbp[2]);
+                sdw = fmaf(S.dw[0][ii], sdot, sdw);
+                sw = fmaf(S.w[0][ii], sdot, sw);
             }
+            xbp[0] = fmaf(wyz, sdw, xbp[0]);
+            xbp[1] = fmaf(dwyz, sw, xbp[1]);
+            xbp[2] = fmaf(wydz, sw, xbp[2]);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 Ab[3 * a] += R1[a];
