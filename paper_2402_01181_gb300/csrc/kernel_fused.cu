@@ -82,7 +82,10 @@ struct FusedSmem {
     uint32_t cand_start[CMAX];     // first slot of each run
     uint32_t cand_pre[CMAX + 1];   // exclusive prefix of run lengths
     uint32_t lane_first[27], lane_off[27];
-    uint32_t wcnt[2][NW][28];      // per pass parity: per-warp direction counts
+    // per pass parity: per direction, each warp's count of it (one byte per
+    // warp, so that a lane sums all warps' counts of its direction in one load)
+    static constexpr int NWP = NW <= 4 ? 4 : 8;
+    alignas(8) uint8_t wcnt[2][28][NWP];
     uint32_t ncand, total, out_base, chunk_first, npass, mask, bmax, wide;
 };
 
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
             }
         }
         if (tid < 32) s.ccount[tid] = 0u;
-        for (int q = tid; q < 2 * NW * 28; q += T) (&s.wcnt[0][0][0])[q] = 0u;
+        for (int q = tid; q < 2 * 28 * Smem::NWP / 4; q += T) reinterpret_cast<uint32_t *>(&s.wcnt[0][0][0])[q] = 0u;
         if (tid == T - 1) {
             s.items[cb ^ 1] = next_item;
             s.bids[cb ^ 1] = item_block(next_item);
@@ -562,17 +565,24 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
             // barrier per pass; warp 0 also publishes the pass's runs)
             const unsigned peers = __match_any_sync(0xffffffffu, d);
             const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-            uint32_t(*wc)[28] = s.wcnt[pass & 1];
-            if (valid && rank == 0) wc[warp][d] = __popc(peers);
+            uint8_t(*wc)[Smem::NWP] = s.wcnt[pass & 1];
+            if (valid && rank == 0) wc[d][warp] = (uint8_t)__popc(peers);
             __syncthreads();
             const uint32_t out_base = s.out_base, chunk_first = s.chunk_first;
             uint32_t run = 0, before = 0;                 // lane l: pass total and earlier warps' count of direction l
             if (lane < 27) {
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    const uint32_t c = wc[w][lane];
-                    before += w < warp ? c : 0u;
-                    run += c;
+                // byte sums by one multiply (four counts of at most 32: no carries)
+                auto bsum = [](uint32_t x) { return (x * 0x01010101u) >> 24; };
+                if (Smem::NWP == 8) {
+                    const uint2 c = *reinterpret_cast<const uint2 *>(&wc[lane][0]);
+                    const uint32_t mlo = warp >= 4 ? 0xffffffffu : (1u << (8 * warp)) - 1u;
+                    const uint32_t mhi = warp <= 4 ? 0u : (1u << (8 * (warp - 4))) - 1u;
+                    run = bsum(c.x) + bsum(c.y);
+                    before = bsum(c.x & mlo) + bsum(c.y & mhi);
+                } else {
+                    const uint32_t c = *reinterpret_cast<const uint32_t *>(&wc[lane][0]);
+                    run = bsum(c);
+                    before = bsum(c & ((1u << (8 * warp)) - 1u));
                 }
             }
             uint32_t incl = run;
@@ -582,9 +592,9 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
                 if (lane >= o) incl += y;
             }
             const uint32_t my_off = __shfl_sync(0xffffffffu, incl - run + before, d & 31);
-            // this warp's row of the other parity is next written by this warp, in the
-            // next pass; every warp's reads of it ended before the barrier above
-            if (lane < 28) s.wcnt[(pass + 1) & 1][warp][lane] = 0u;
+            // this warp's column of the other parity is next written by this warp, in
+            // the next pass; every warp's reads of it ended before the barrier above
+            if (lane < 28) s.wcnt[(pass + 1) & 1][lane][warp] = 0u;
             if (warp == 0 && chunk_first + pass < nchunk_cap) {
                 const uint32_t pbase = out_base + pass * T;
                 if (lane < 27) {
