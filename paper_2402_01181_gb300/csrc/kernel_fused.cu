@@ -121,6 +121,11 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool va
     const int bytes = valid ? 16 : 0;   // 0: fill with zeros, read nothing
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem), "r"(bytes) : "memory");
 }
+// 16 bytes into shared memory without allocating in L1 (streamed particle state)
+__device__ __forceinline__ void cp_async16_cg(void *smem, const void *gmem) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem) : "memory");
@@ -145,9 +150,9 @@ __device__ __forceinline__ uint32_t source_slot(const Smem &s, uint32_t ncand, u
 template <class Smem>
 __device__ __forceinline__ void prefetch_particle(Smem &s, const PState &in, uint32_t ncand, uint32_t j, int tid) {
     const uint32_t src = source_slot(s, ncand, j);
-    cp_async16(&s.pxi[tid], &in.xi[src], true);
-    cp_async16(&s.pf0[tid], &in.f0[src], true);
-    cp_async16(&s.pf1[tid], &in.f1[src], true);
+    cp_async16_cg(&s.pxi[tid], &in.xi[src]);
+    cp_async16_cg(&s.pf0[tid], &in.f0[src]);
+    cp_async16_cg(&s.pf1[tid], &in.f1[src]);
     cp_async4(&s.pf2[tid], &in.f2[src]);
 }
 
