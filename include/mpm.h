@@ -265,9 +265,9 @@ mpm_status mpm_extract_surface(mpm_handle *h, int32_t env, float iso, float *tri
 enum {
     MPM_KERNEL_T256_G2 = 0, /* 256 threads, 512 particles per flush (the default) */
     MPM_KERNEL_T256_G1 = 1, /* 256 threads, 256 particles per flush */
-    MPM_KERNEL_T128_G2 = 2, /* 128 threads, 256 particles per flush */
+    MPM_KERNEL_T128_G2 = 2, /* 128 threads, 256 particles per flush, particles copied 2 passes ahead */
     MPM_KERNEL_T128_G1 = 3, /* 128 threads, 128 particles per flush */
-    MPM_KERNEL_T256_G2_C2 = 4, /* 256 threads, 512 particles per flush, 2 CTAs per SM */
+    MPM_KERNEL_T256_G2_C2 = 4, /* 256 threads, 512 particles per flush, 2 CTAs per SM, copied 2 passes ahead */
     MPM_KERNEL_CONFIGS = 5
 };
 

@@ -51,7 +51,9 @@ constexpr int kAy = 8, kAz = 68, kArena = 8 * kAz;
 
 // Shared memory of a CTA of T threads that stages GP passes (GP T particles)
 // per arena flush.
-template <int T, int GP>
+// PD: particle copies in flight per thread (a pass's particle is copied PD
+// passes ahead of its use)
+template <int T, int GP, int PD = 1>
 struct FusedSmem {
     static constexpr int NW = T / 32;
     static constexpr int GROUP = GP * T;
@@ -77,8 +79,8 @@ struct FusedSmem {
     float st_a[9][GROUP];
     // each thread's particle of the current pass, prefetched with cp.async a pass
     // ahead (a thread reads and refills only its own slot)
-    float4 pxi[T], pf0[T], pf1[T];
-    float pf2[T];
+    float4 pxi[PD][T], pf0[PD][T], pf1[PD][T];
+    float pf2[PD][T];
     uint32_t cand_start[CMAX];     // first slot of each run
     uint32_t cand_pre[CMAX + 1];   // exclusive prefix of run lengths
     uint32_t lane_first[27], lane_off[27];
@@ -96,6 +98,8 @@ constexpr int kMinBlocks = T == 256 ? 3 : (GP == 1 ? 5 : 4);
 static_assert(3 * (sizeof(FusedSmem<256, 2>) + 1024) <= 228 * 1024, "shared memory for three CTAs per SM");
 static_assert(4 * (sizeof(FusedSmem<128, 2>) + 1024) <= 228 * 1024, "shared memory for four CTAs per SM");
 static_assert(5 * (sizeof(FusedSmem<128, 1>) + 1024) <= 228 * 1024, "shared memory for five CTAs per SM");
+static_assert(4 * (sizeof(FusedSmem<128, 2, 2>) + 1024) <= 228 * 1024, "configuration 2: four CTAs per SM");
+static_assert(2 * (sizeof(FusedSmem<256, 2, 2>) + 1024) <= 228 * 1024, "configuration 4: two CTAs per SM");
 
 __device__ __forceinline__ int dir_dx(int d) { return d % 3 - 1; }
 __device__ __forceinline__ int dir_dy(int d) { return (d / 3) % 3 - 1; }
@@ -133,6 +137,7 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_but_two() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 
 // Slot of logical index j among the block's incoming runs (binary search of
 // the runs' exclusive prefix).
@@ -148,12 +153,13 @@ __device__ __forceinline__ uint32_t source_slot(const Smem &s, uint32_t ncand, u
 
 // Start copying the particle with logical index j into this thread's slot.
 template <class Smem>
-__device__ __forceinline__ void prefetch_particle(Smem &s, const PState &in, uint32_t ncand, uint32_t j, int tid) {
+__device__ __forceinline__ void prefetch_particle(Smem &s, const PState &in, uint32_t ncand, uint32_t j, int tid,
+                                                  int set) {
     const uint32_t src = source_slot(s, ncand, j);
-    cp_async16_cg(&s.pxi[tid], &in.xi[src]);
-    cp_async16_cg(&s.pf0[tid], &in.f0[src]);
-    cp_async16_cg(&s.pf1[tid], &in.f1[src]);
-    cp_async4(&s.pf2[tid], &in.f2[src]);
+    cp_async16_cg(&s.pxi[set][tid], &in.xi[src]);
+    cp_async16_cg(&s.pf0[set][tid], &in.f0[src]);
+    cp_async16_cg(&s.pf1[set][tid], &in.f1[src]);
+    cp_async4(&s.pf2[set][tid], &in.f2[src]);
 }
 
 // Start copying global block b's grid region of G_k, its inbox, and its
@@ -195,11 +201,12 @@ __device__ __forceinline__ void prefetch_block(Smem &s, int buf, uint32_t b, con
 // block's output was allocated) with their input positions, the list of
 // blocks in work order with each one's range, the list's length, and the grid
 // of each block's region before and after the grid operation.
-template <bool WRITE_VC, int T, int GP, int MINB = kMinBlocks<T, GP>, bool RECORD = false>
+template <bool WRITE_VC, int T, int GP, int MINB = kMinBlocks<T, GP>, bool RECORD = false, int PD = 1>
 __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B,
                                                                      const ToolFrame *__restrict__ tools,
                                                                      StepRecord rec) {
-    using Smem = FusedSmem<T, GP>;
+    using Smem = FusedSmem<T, GP, PD>;
+    static_assert(PD == 1 || PD == 2, "one or two particle copies in flight");
     constexpr int NW = Smem::NW, GROUP = Smem::GROUP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &s = *reinterpret_cast<Smem *>(smem_raw);
@@ -394,8 +401,12 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
         }
         // this thread's particle of the first pass, then the next block's inputs;
         // both land while this block computes
-        if (npass > 0 && (uint32_t)tid < total) prefetch_particle(s, in, ncand, (uint32_t)tid, tid);
+        if (npass > 0 && (uint32_t)tid < total) prefetch_particle(s, in, ncand, (uint32_t)tid, tid, 0);
         cp_async_commit();
+        if (PD == 2) {   // and the second pass's
+            if (npass > 1 && (uint32_t)(T + tid) < total) prefetch_particle(s, in, ncand, (uint32_t)(T + tid), tid, 1);
+            cp_async_commit();
+        }
         if (s.items[cb ^ 1] < nact) prefetch_block<T>(s, cb ^ 1, s.bids[cb ^ 1], inbox_in, Gcur, P, tools, tid);
         else cp_async_commit();
         const int ox = 4 * bx - 1, oy = 4 * by - 1, oz = 4 * bz - 1;   // arena origin
@@ -407,11 +418,19 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
             int d = 31;
             float nxp = 0.f, nyp = 0.f, nzp = 0.f, idf = 0.f, Fn[9], Cm[9], vx = 0.f, vy = 0.f, vz = 0.f;
             // this pass's particle is in the slot; the next block's inputs may still be landing
-            if (pass == 0) cp_async_wait_but_one(); else cp_async_wait_all();
+            // every thread commits, in order: pass 0's particle, [PD = 2: pass 1's
+            // particle,] the next block's inputs, then one group per pass holding
+            // the particle of pass + PD.  Wait for this pass's particle only.
+            if (PD == 1) {
+                if (pass == 0) cp_async_wait_but_one(); else cp_async_wait_all();
+            } else {
+                if (pass <= 1) cp_async_wait_but_two(); else cp_async_wait_but_one();
+            }
             float4 xi = make_float4(0.f, 0.f, 0.f, 0.f), a0 = xi, a1 = xi;
             float f2 = 0.f;
-            if (valid) { xi = s.pxi[tid]; a0 = s.pf0[tid]; a1 = s.pf1[tid]; f2 = s.pf2[tid]; }
-            const uint32_t jn = j + T;
+            const int ps = (int)(pass % PD);   // slot set of this pass's particle
+            if (valid) { xi = s.pxi[ps][tid]; a0 = s.pf0[ps][tid]; a1 = s.pf1[ps][tid]; f2 = s.pf2[ps][tid]; }
+            const uint32_t jn = j + PD * T;
             if (valid) {
                 const float F[9] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w, f2};
                 idf = xi.w;
@@ -489,7 +508,7 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
                 nzp = xi.z + P.dt * vz;
                 // every value read from the slot has been consumed: refill it with the
                 // next pass's particle
-                if (pass + 1 < npass && jn < total) prefetch_particle(s, in, ncand, jn, tid);
+                if (pass + PD < npass && jn < total) prefetch_particle(s, in, ncand, jn, tid, ps);
                 if (!finite3(nxp, nyp, nzp)) {
                     err |= kErrNumeric;
                     nxp = xi.x; nyp = xi.y; nzp = xi.z;
@@ -795,24 +814,24 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
     }
 }
 
-template <int T, int GP, int MINB = kMinBlocks<T, GP>>
+template <int T, int GP, int MINB = kMinBlocks<T, GP>, int PD = 1>
 void launch_variant(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, bool write_vc, int grid,
                     cudaStream_t st) {
     const StepRecord none{};
     if (write_vc)
-        k_fused_step<true, T, GP, MINB><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools, none);
+        k_fused_step<true, T, GP, MINB, false, PD><<<grid, T, sizeof(FusedSmem<T, GP, PD>), st>>>(P, B, tools, none);
     else
-        k_fused_step<false, T, GP, MINB><<<grid, T, sizeof(FusedSmem<T, GP>), st>>>(P, B, tools, none);
+        k_fused_step<false, T, GP, MINB, false, PD><<<grid, T, sizeof(FusedSmem<T, GP, PD>), st>>>(P, B, tools, none);
 }
 
-template <int T, int GP, int MINB = kMinBlocks<T, GP>>
+template <int T, int GP, int MINB = kMinBlocks<T, GP>, int PD = 1>
 int variant_occupancy() {
-    const int bytes = (int)sizeof(FusedSmem<T, GP>);
-    cudaFuncSetAttribute(k_fused_step<true, T, GP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_fused_step<false, T, GP, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const int bytes = (int)sizeof(FusedSmem<T, GP, PD>);
+    cudaFuncSetAttribute(k_fused_step<true, T, GP, MINB, false, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_fused_step<false, T, GP, MINB, false, PD>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fused_step<true, T, GP, MINB>, T, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_step<false, T, GP, MINB>, T, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fused_step<true, T, GP, MINB, false, PD>, T, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_step<false, T, GP, MINB, false, PD>, T, bytes);
     return a < b ? a : b;
 }
 
@@ -822,9 +841,9 @@ void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *
                        int config, cudaStream_t st) {
     switch (config) {
     case 1: launch_variant<256, 1>(P, B, tools, write_vc, grid, st); break;
-    case 2: launch_variant<128, 2>(P, B, tools, write_vc, grid, st); break;
+    case 2: launch_variant<128, 2, kMinBlocks<128, 2>, 2>(P, B, tools, write_vc, grid, st); break;
     case 3: launch_variant<128, 1>(P, B, tools, write_vc, grid, st); break;
-    case 4: launch_variant<256, 2, 2>(P, B, tools, write_vc, grid, st); break;   // 2 CTAs per SM, 128 registers
+    case 4: launch_variant<256, 2, 2, 2>(P, B, tools, write_vc, grid, st); break;   // 2 CTAs per SM, 128 registers
     default: launch_variant<256, 2>(P, B, tools, write_vc, grid, st); break;
     }
 }
@@ -851,9 +870,9 @@ void launch_fused_step_record(const DevParams &P, const FusedBufs &B, const Tool
 int fused_step_occupancy(int config) {
     switch (config) {
     case 1: return variant_occupancy<256, 1>();
-    case 2: return variant_occupancy<128, 2>();
+    case 2: return variant_occupancy<128, 2, kMinBlocks<128, 2>, 2>();
     case 3: return variant_occupancy<128, 1>();
-    case 4: return variant_occupancy<256, 2, 2>();
+    case 4: return variant_occupancy<256, 2, 2, 2>();
     default: return variant_occupancy<256, 2>();
     }
 }

@@ -171,7 +171,8 @@ struct ReverseArgs {
     uint32_t *touch_n;         // receives the number of work-list blocks (do_g2p)
 };
 // config (MPM_KERNEL_*): 0 = 256 threads, 2 passes per P2G flush; 1 = 256, 1;
-// 2 = 128, 2; 3 = 128, 1
+// 2 = 128, 2; 3 = 128, 1; 4 = 256, 2 with 2 CTAs per SM.  Configurations 2 and
+// 4 copy each pass's particles two passes ahead, the others one pass ahead.
 void launch_fused_step(const DevParams &P, const FusedBufs &B, const ToolFrame *tools, bool write_vc, int grid,
                        int config, cudaStream_t st);
 int fused_step_occupancy(int config);
