@@ -109,21 +109,47 @@ def _suite(name):
     return PINS["forward"]
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_pins_catch_planted_mistake(name, tmp_path):
+def _run_c_mutant(name, work):
+    """Build the oracle with planted mistake `name` and run its pin suite;
+    returns (anchor found once, pin-suite exit code, output)."""
     old, new = MUTATIONS[name]
     src = open(SRC).read()
-    assert src.count(old) == 1, "mutation anchor must be unique: " + name
-    mutated = tmp_path / "mut.c"
-    mutated.write_text(src.replace(old, new))
-    lib = tmp_path / "libmut.so"
+    if src.count(old) != 1:
+        return False, None, ""
+    os.makedirs(work, exist_ok=True)
+    mutated = os.path.join(work, "mut.c")
+    with open(mutated, "w") as fh:
+        fh.write(src.replace(old, new))
+    lib = os.path.join(work, "libmut.so")
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                           "-o", str(lib), str(mutated), "-lm"])
-    env = dict(os.environ, ORACLE_LIB=str(lib))
+                           "-o", lib, mutated, "-lm"])
+    env = dict(os.environ, ORACLE_LIB=lib)
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", _suite(name))],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, "planted mistake '%s' passed every pin" % name
+    return True, r.returncode, r.stdout[-2000:] + r.stderr[-2000:]
+
+
+def _in_parallel(fn, names, base):
+    """fn(name, work dir) for every name, the independent child processes
+    running side by side on the host's cores."""
+    from concurrent.futures import ThreadPoolExecutor
+    workers = max(1, min(len(names), os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {n: ex.submit(fn, n, os.path.join(str(base), "m%02d" % i)) for i, n in enumerate(names)}
+        return {n: f.result() for n, f in futs.items()}
+
+
+@pytest.fixture(scope="module")
+def c_mutants(tmp_path_factory):
+    return _in_parallel(_run_c_mutant, sorted(MUTATIONS), tmp_path_factory.mktemp("c_mutants"))
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, c_mutants):
+    unique, rc, out = c_mutants[name]
+    assert unique, "mutation anchor must be unique: " + name
+    assert rc != 0, "planted mistake '%s' passed every pin" % name
 
 
 PY_SRC = os.path.join(ROOT, "oracle", "oracle.py")
@@ -153,16 +179,34 @@ sys.exit(pytest.main(["-q", "-x", "-p", "no:cacheprovider", %r]))
 """
 
 
-@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
-def test_pins_catch_planted_python_mistake(name, tmp_path):
+def _run_py_mutant(name, work):
+    """Load oracle/oracle.py with planted mistake `name` in a child process
+    and run its pin suite; returns (anchor found once, exit code, output)."""
     from oracle import oracle as O
     old, new = PY_MUTATIONS[name]
     src = open(PY_SRC).read()
-    assert src.count(old) == 1, "mutation anchor must be unique: " + name
-    mutated = tmp_path / "oracle.py"
-    mutated.write_text(src.replace(old, new))
+    if src.count(old) != 1:
+        return False, None, ""
+    os.makedirs(work, exist_ok=True)
+    mutated = os.path.join(work, "oracle.py")
+    with open(mutated, "w") as fh:
+        fh.write(src.replace(old, new))
     env = dict(os.environ, ORACLE_LIB=O.build())
-    code = _DRIVER % (ROOT, str(mutated), os.path.join(ROOT, "tests", _suite(name)))
+    code = _DRIVER % (ROOT, mutated, os.path.join(ROOT, "tests", _suite(name)))
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr
-    assert r.returncode != 0, "planted mistake '%s' passed every pin" % name
+    return True, r.returncode, r.stdout + r.stderr
+
+
+@pytest.fixture(scope="module")
+def py_mutants(tmp_path_factory):
+    from oracle import oracle as O
+    O.build()                    # once, before the children share the library
+    return _in_parallel(_run_py_mutant, sorted(PY_MUTATIONS), tmp_path_factory.mktemp("py_mutants"))
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_pins_catch_planted_python_mistake(name, py_mutants):
+    unique, rc, out = py_mutants[name]
+    assert unique, "mutation anchor must be unique: " + name
+    assert "passed" in out or "failed" in out, out
+    assert rc != 0, "planted mistake '%s' passed every pin" % name
