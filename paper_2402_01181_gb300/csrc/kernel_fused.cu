@@ -794,8 +794,11 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
     if (err) atomicOr(&ctrl->err, err);
     // last CTA: reset per-launch counters, advance the sub-step
     __syncthreads();
+    // No fence before the done counter: the last CTA reads only part_alloc,
+    // whose atomics every CTA consumed (its block's output range) before
+    // counting itself done, and everything it writes is read by the next
+    // launch, after this one has completed.
     if (tid == 0) {
-        __threadfence();
         const uint32_t prev = atomicAdd(&ctrl->done, 1u);
         if (prev == gridDim.x - 1) {
             __threadfence();
@@ -807,7 +810,6 @@ __global__ void __launch_bounds__(T, MINB) k_fused_step(DevParams P, FusedBufs B
             ctrl->nactive[par][1] = 0;
             ctrl->nclear[m3c] = 0;
             ctrl->done = 0;
-            __threadfence();
             if (RECORD) *rec.nact = nact;
             ctrl->step = step + 1;
         }
